@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Benchmark of the particle-in-cell step on one GB300 (or N replicas).
+
+Default workload: 3D3V periodic thermal pair plasma, 128^3 cells, 32
+particles per cell per species (134,217,728 particles), theta = 1, n_x = 1,
+rho_sp0 = 64, dt = 0.5.  A step is one full main-loop step of App. A.3.1:
+field half advances, gather + Boris + move + charge-conserving deposit,
+e advance with the current, and the amortised re-sort.  The metric is
+particle-steps per nanosecond of the mixed-precision path; the FP64 path is
+timed on the same workload next to it.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload (a 32^3 box with the same particles per
+cell and temperature).  Multi-GPU: the runs are independent replicas, one per
+rank, with no collective on the data path.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "thermal3d_128": dict(name="3D3V thermal pair plasma 128^3, 32 ppc/species, theta=1", ndim=3, nx=128, ny=128,
+                          nz=128, ppc=32, theta=1.0, n_x=1.0, rho_sp0=64.0, dt=0.5),
+    "thermal2d_1024": dict(name="2D3V thermal pair plasma 1024^2, 50 ppc/species, theta=0.01", ndim=2, nx=1024,
+                           ny=1024, nz=1, ppc=50, theta=0.01, n_x=20.0, rho_sp0=100.0, dt=0.5),
+    "thermal2d_64": dict(name="2D3V thermal pair plasma 64^2, 16 ppc/species, theta=0.1", ndim=2, nx=64, ny=64, nz=1,
+                         ppc=16, theta=0.1, n_x=0.1 ** -0.5, rho_sp0=32.0, dt=0.5),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _host_state(w, seed, chunk=1 << 24):
+    """Seeded synthetic state: co-located pairs (rho = 0), uniform positions,
+    momenta drawn per component from a normal of variance theta (a stand-in
+    for the thermal spread; the exact Maxwell-Juttner loader lives in the
+    library), zero fields."""
+    rng = np.random.default_rng(seed)
+    nz = 1 if w["ndim"] == 2 else w["nz"]
+    ncell = w["nx"] * w["ny"] * nz
+    n = int(w["ppc"] * ncell)
+    pos = np.zeros((3, n))
+    for a, L in enumerate((w["nx"], w["ny"], nz)[: w["ndim"]]):
+        pos[a] = rng.uniform(0.0, L, n)
+        np.minimum(pos[a], np.nextafter(L, 0.0), out=pos[a])
+    parts = []
+    for s in range(2):
+        p = np.empty((6, n))
+        p[:3] = pos
+        p[3:] = rng.normal(0.0, np.sqrt(w["theta"]), (3, n))
+        parts.append(p)
+    fields = np.zeros((6, nz, w["ny"], w["nx"]))
+    return fields, parts, n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _time_oracle_sample(w, steps, seed):
+    """FP64 oracle on a 32^3 (3D) or 64^2 (2D) box with the workload's ppc and
+    temperature; returns (particle-steps/ns, seconds, particles, steps)."""
+    import oracle
+    sw = dict(w)
+    if w["ndim"] == 3:
+        sw.update(nx=32, ny=32, nz=32)
+    else:
+        sw.update(nx=min(w["nx"], 64), ny=min(w["ny"], 64))
+    fields, parts, n = _host_state(sw, seed)
+    st = oracle.State.empty(w["ndim"], sw["nx"], sw["ny"], sw["nz"], w["dt"], w["n_x"], w["rho_sp0"])
+    for s, q in enumerate((-1.0, 1.0)):
+        st.species.append(oracle.Species(np.ascontiguousarray(parts[s][:3]), np.ascontiguousarray(parts[s][3:]), q, 1.0))
+    t0 = time.perf_counter()
+    oracle.step(st, steps)
+    dt = time.perf_counter() - t0
+    ps = 2 * n * steps
+    return ps / (dt * 1e9), dt, 2 * n, steps, sw
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = []
+    for k in range(args.warmup + args.steps):
+        v, dt, npart, nst, sw = _time_oracle_sample(w, 1, seed=1000 + k)
+        if k >= args.warmup:
+            times.append(dt)
+    npart_steps = npart * args.steps
+    total = sum(times)
+    val = npart_steps / (total * 1e9)
+    sample = "FP64 oracle, 1 step per timed step on a %dx%dx%d box, %d ppc/species, theta=%g (%d particles)" % (
+        sw["nx"], sw["ny"], sw["nz"] if w["ndim"] == 3 else 1, w["ppc"], w["theta"], npart)
+    out = {"impl": "reference", "metric": "particle-steps/ns", "value": val, "unit": "particle-steps/ns",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w["name"], "sample": sample},
+           "cpu_baseline": {"value": val, "unit": "particle-steps/ns", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "particle-steps/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args, w):
+    import torch
+    import paper_1308_5892_gb300 as pic
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    fields, parts, n = _host_state(w, seed=2 + rank)
+    nz = 1 if w["ndim"] == 2 else w["nz"]
+    desc = pic.run_desc(w["ndim"], w["nx"], w["ny"], nz, w["n_x"], w["rho_sp0"], w["dt"],
+                        [(-1.0, 1.0, n), (1.0, 1.0, n)])
+    npart = 2 * n
+    results = {}
+    for prec, name in ((pic.PIC_MIXED, "mixed"), (pic.PIC_FP64, "fp64")):
+        steps = args.steps if prec == pic.PIC_MIXED else max(1, min(args.steps, args.fp64_steps))
+        ctx = pic.Context([desc], precision=prec, flags=pic.PIC_FLAG_TIMING)
+        ctx.set_state(0, fields, parts)
+        ctx.step(args.warmup)
+        ctx.kernel_time(pic.PIC_KERNEL_PUSH, reset=True)
+        stream = torch.cuda.current_stream()
+        barrier()
+        clocks = ClockSampler(local)
+        if prec == pic.PIC_MIXED:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(steps)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop() if prec == pic.PIC_MIXED else None
+        push_ms, push_n = ctx.kernel_time(pic.PIC_KERNEL_PUSH)
+        field_ms, field_n = ctx.kernel_time(pic.PIC_KERNEL_FIELD)
+        sort_ms, sort_n = ctx.kernel_time(pic.PIC_KERNEL_SORT, reset=True)
+        cnt = ctx.counters()
+        diag = ctx.diagnostics(0)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        results[name] = dict(ms=ms, steps=steps, push_ms=push_ms, push_n=push_n, field_ms=field_ms,
+                             sort_ms=sort_ms, counters=cnt, clocks=clk, diag=diag,
+                             tuning=ctx.tuning() if prec == pic.PIC_MIXED else None)
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+
+    # end-to-end through the C ABI with host buffers: upload the state, run the
+    # timed steps, read the state back; all copies inside the timed region
+    pin_f = torch.from_numpy(fields).pin_memory().numpy()
+    pin_p = [torch.from_numpy(p).pin_memory().numpy() for p in parts]
+    out_f = torch.empty(fields.shape, dtype=torch.float64).pin_memory().numpy()
+    out_p = [torch.empty(p.shape, dtype=torch.float64).pin_memory().numpy() for p in parts]
+    ctx = pic.Context([desc], precision=pic.PIC_MIXED)
+    ctx.set_state(0, pin_f, pin_p)
+    ctx.step(args.warmup)
+    barrier()
+    t0 = time.perf_counter()
+    ctx.set_state(0, pin_f, pin_p)
+    ctx.step(args.steps)
+    ctx.get_state(0, out=(out_f, out_p))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    ctx.close()
+    h2d = fields.nbytes + sum(p.nbytes for p in parts)
+    d2h = h2d
+
+    m = results["mixed"]
+    value_rank = npart * m["steps"] / (m["ms"] * 1e6)
+    value = value_rank * world
+    f64 = results["fp64"]
+    peak, peak_kind = _peaks()
+    push_launch_ms = m["push_ms"] / max(m["push_n"], 1)
+    bytes_per_launch = m["counters"]["bytes_per_particle_step"] * npart
+    achieved = bytes_per_launch / (push_launch_ms * 1e-3) / 1e9
+    if rank == 0:
+        out = {
+            "metric": "particle-steps/ns", "value": value, "unit": "particle-steps/ns", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / m["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32 (mixed); f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "particles_per_gpu": npart, "cells": w["nx"] * w["ny"] * (w["nz"] if w["ndim"] == 3 else 1),
+                       "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 (%.1f GB particle state)" % (npart * 28 / 1e9),
+                       "tuning": m["tuning"]},
+            "fp64": {"value": npart * f64["steps"] / (f64["ms"] * 1e6) * world, "unit": "particle-steps/ns",
+                     "ms_per_step": f64["ms"] / f64["steps"], "steps": f64["steps"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_push_mixed (gather+push+deposit, both species)",
+                         "peak_kind": peak_kind, "push_ms_per_step": push_launch_ms,
+                         "field_ms_per_step": m["field_ms"] / m["steps"], "sort_ms_total": m["sort_ms"]},
+            "cpu_baseline": None,
+            "e2e": {"value": npart * args.steps / (e2e_s * 1e9) * world, "unit": "particle-steps/ns",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "note": "set_state from pinned host + steps + get_state to pinned host"},
+            "gpu_launches": int(m["counters"]["launches_per_step"] * m["steps"]),
+            "clocks": m["clocks"],
+            "diag": {"gauss_max": m["diag"]["gauss_max"], "rho_max": m["diag"]["rho_max"]},
+        }
+        if not args.no_cpu_baseline:
+            v, dt, npp, nst, sw = _time_oracle_sample(w, 1, seed=77)
+            out["cpu_baseline"] = {"value": v, "unit": "particle-steps/ns", "cores": 1, "kind": "oracle",
+                                   "sample": "1 step of the FP64 oracle on a %dx%dx%d box with the same ppc and theta "
+                                             "(%d particles, %.1f s)" % (sw["nx"], sw["ny"], sw["nz"] if w["ndim"] == 3 else 1, npp, dt)}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="thermal3d_128", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+/*
+ * pic.h -- C ABI of the GB300 particle-in-cell step library (libpic_gb300.so).
+ *
+ * The library advances the particle-in-cell scheme of Apar-T (Melzani et al.,
+ * arXiv 1308.5892, Sect. 2 and App. A) on one NVIDIA GB300 GPU (sm_103a):
+ * field gather from the staggered Yee grid, relativistic Boris push and
+ * position update, charge-conserving current deposition by volume change,
+ * and the FDTD Maxwell update.  All quantities are in the paper's normalised
+ * units (App. A.2): cell size X0 = 1, time in X0/c, velocities in c, fields
+ * e and b = cB in m_e c^2/(e X0), momenta u = gamma v / c.
+ *
+ * General conventions
+ *  - Every call returns a pic_status; nothing aborts or throws across the ABI.
+ *    On failure pic_last_error(ctx) holds a one-line message.
+ *  - Invalid arguments give PIC_EINVAL before any device work is queued.
+ *  - Host pointers are borrowed for the duration of the call only.
+ *  - Device memory belongs to the context.  It is obtained through the
+ *    caller's pic_allocator (or cudaMalloc when none is given) inside
+ *    pic_init and returned in pic_destroy; no other call allocates, except
+ *    the loader's temporary lookup table (freed before it returns).
+ *  - Device work is queued on the stream given in pic_opts (NULL: the legacy
+ *    default stream).  Calls that return data to the host synchronise that
+ *    stream; pic_step synchronises it unless PIC_FLAG_ASYNC is set.
+ *  - A context is used from one host thread at a time.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_MAX_SPECIES 4
+#define PIC_ABI_VERSION 1
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,    /* invalid argument or descriptor */
+    PIC_ENOMEM = 2,    /* the allocator returned NULL */
+    PIC_ECUDA = 3,     /* a CUDA runtime call failed (message names it) */
+    PIC_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    PIC_ENUMERIC = 5,  /* a non-finite value was found in the state */
+    PIC_ESTATE = 6     /* call not valid in the current state, or a particle
+                          moved farther than one cell in one step */
+} pic_status;
+
+typedef enum { PIC_FP64 = 0, PIC_MIXED = 1 } pic_precision;
+typedef enum { PIC_BC_PERIODIC = 0, PIC_BC_CONDUCTOR = 1 } pic_bc;
+typedef enum { PIC_PROFILE_UNIFORM = 0, PIC_PROFILE_HARRIS = 1 } pic_profile;
+typedef enum { PIC_MJ_EXACT = 0, PIC_MJ_MLP = 1, PIC_MJ_NAIVE_BOOST = 2 } pic_mj_method;
+
+#define PIC_FLAG_ASYNC 1u      /* pic_step returns without synchronising */
+#define PIC_FLAG_NO_GRAPH 2u   /* pic_step launches kernels directly instead of replaying a CUDA graph */
+#define PIC_FLAG_TIMING 4u     /* record CUDA events around each kernel class (see pic_kernel_time) */
+
+/* Kernel classes timed under PIC_FLAG_TIMING. */
+typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_FIELD = 1, PIC_KERNEL_SORT = 2 } pic_kernel_class;
+
+/* Device memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes aligned to 256 bytes, or NULL; free receives the same pointer and size. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, size_t bytes, void *user);
+    void *user;
+} pic_allocator;
+
+/* One superparticle species (Sect. 2.1): charge and mass of the real particle
+ * in units of e and m_e; every superparticle has the same weight.  capacity is
+ * the maximum number of superparticles the run will hold. */
+typedef struct {
+    double q_over_e;
+    double m_over_me;
+    int64_t capacity;
+} pic_species_desc;
+
+/* One simulation (Sect. 2.2.1 and App. A.2).
+ *  ndim      2 (2D3V: z ignorable, particles carry u_z) or 3
+ *  nx,ny,nz  cells per axis (nz = 1 when ndim = 2); 2..2047 each, nx,ny <= 65535 in 2D
+ *  n_x       cells per electron skin depth
+ *  rho_sp0   reference superparticles per cell, all species together; with
+ *            n_x it fixes the current coupling alpha_s = 2 sgn(q_s)/(n_x^2 rho_sp0) (Eq. alpha)
+ *  dt        time step in X0/c; must satisfy dt < 1/sqrt(ndim) (Courant, App. B.1)
+ *  bc        per axis: PIC_BC_PERIODIC, or PIC_BC_CONDUCTOR for x only (App. A.4) */
+typedef struct {
+    int ndim;
+    int nx, ny, nz;
+    double n_x;
+    double rho_sp0;
+    double dt;
+    int bc[3];
+    int nspecies;
+    pic_species_desc species[PIC_MAX_SPECIES];
+} pic_run_desc;
+
+/* Options of a context.
+ *  precision      PIC_FP64: every quantity in double precision, plain
+ *                 one-thread-per-particle kernel with global atomics.
+ *                 PIC_MIXED: positions as cell index + FP32 offset, FP32
+ *                 momenta and fields, currents accumulated in FP32 with
+ *                 compensated summation in shared memory, particles kept
+ *                 sorted by tile; FP64 for diagnostics.
+ *  sort_interval  steps between re-sorts in PIC_MIXED (0: chosen by the autotuner)
+ *  tile           tile shape in cells (0: chosen by the autotuner)
+ *  stream         cudaStream_t to queue work on (NULL: default stream)
+ *  allocator      device memory provider (NULL: cudaMalloc/cudaFree)
+ *  flags          PIC_FLAG_* bits */
+typedef struct {
+    int precision;
+    int sort_interval;
+    int tile[3];
+    void *stream;
+    const pic_allocator *allocator;
+    uint32_t flags;
+} pic_opts;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Host view of one run's state at the start of a step (App. A.3.1):
+ * positions x^t, momenta u^{t-dt/2}, e^t, b^{t-dt/2}.
+ *  fields        6 * ncell doubles: planes e_x, e_y, e_z, b_x, b_y, b_z, each
+ *                ncell = nz*ny*nx values indexed (k*ny + j)*nx + i, with the
+ *                Yee staggering e_x (i+1/2,j,k), e_y (i,j+1/2,k), e_z (i,j,k+1/2),
+ *                b_x (i,j+1/2,k+1/2), b_y (i+1/2,j,k+1/2), b_z (i+1/2,j+1/2,k)
+ *  count[s]      particles of species s (set: number given; get: in = room in
+ *                the buffer, out = number returned)
+ *  particles[s]  6 * count[s] doubles: planes x, y, z, u_x, u_y, u_z
+ *                (z ignored in 2D); pic_get_state returns particles in the
+ *                order they were given to pic_set_state or loaded
+ *  step          step counter (get only) */
+typedef struct {
+    double *fields;
+    int64_t count[PIC_MAX_SPECIES];
+    double *particles[PIC_MAX_SPECIES];
+    int64_t step;
+} pic_state_view;
+
+/* FP64 diagnostics of one run (Sect. 3.1, App. A.2 units: p m_e c^2 per superparticle).
+ *  kinetic[s]      sum over particles of (m_s/m_e)(gamma - 1), gamma from u^{t-dt/2}
+ *  field_e[c]      |alpha|^-1 sum over cells of e_c^2 / 2 at t
+ *  field_b[c]      |alpha|^-1 sum over cells of b_c^2 / 2 at t - dt/2
+ *  sum_u[s][c]     sum over particles of u_c (= sum gamma v_c, the k = 0
+ *                  momentum of Eq. Fourier)
+ *  temperature[s]  <u . v> / 3 (equals Theta for a Maxwell-Juttner plasma)
+ *  gauss_max       max over nodes of |div e - rho~|, rho~ = sum_s alpha_s W (CIC)
+ *  rho_max         max over species and nodes of |rho~_s|
+ *  nonfinite       number of non-finite values met in fields and particles */
+typedef struct {
+    int64_t step;
+    int nspecies;
+    int64_t count[PIC_MAX_SPECIES];
+    double kinetic[PIC_MAX_SPECIES];
+    double field_e[3];
+    double field_b[3];
+    double sum_u[PIC_MAX_SPECIES][3];
+    double temperature[PIC_MAX_SPECIES];
+    double gauss_max;
+    double rho_max;
+    int64_t nonfinite;
+} pic_diag;
+
+/* ABI version of the loaded library (PIC_ABI_VERSION at build time). */
+int pic_abi_version(void);
+
+/* Create a context holding nruns independent runs (nruns > 1: a batched
+ * ensemble advanced together by pic_step).  Validates every descriptor
+ * (Courant limit, sizes, species count and capacities, boundary kinds) and
+ * returns PIC_EINVAL without touching the device if one is invalid.  Fields
+ * start at zero and every species empty.  *out receives the context, or NULL
+ * on failure. */
+pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, pic_ctx **out);
+
+/* Free all device memory through the allocator and destroy the context. NULL is a no-op. */
+void pic_destroy(pic_ctx *ctx);
+
+/* Message of the last failed call on ctx (empty string if none); valid until the next call. */
+const char *pic_last_error(const pic_ctx *ctx);
+
+/* Upload a state (see pic_state_view).  Positions must lie in the domain,
+ * [0, n) per periodic axis and [0, nx] between conductor walls; counts must
+ * not exceed the capacities.  Non-finite values give PIC_ENUMERIC. */
+pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in);
+
+/* Download the state into caller buffers (converted to FP64). */
+pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out);
+
+/* Add uniform fields e0 to e and b0 to b of one run (tests; background field). */
+pic_status pic_set_uniform_field(pic_ctx *ctx, int run, const double e0[3], const double b0[3]);
+
+/* Load `ppc` superparticles per cell of one species with a drifting
+ * Maxwell-Juttner distribution (Sect. 4.3, Eq. Jutt, App. D) of temperature
+ * theta = T/(m c^2) and bulk velocity beta (in c; |beta| < 1), replacing the
+ * species' particles.  profile: PIC_PROFILE_UNIFORM (uniform density), or
+ * PIC_PROFILE_HARRIS with profile_params[0] = L, [1] = x0: comoving density
+ * proportional to sech^2((x - x0)/L) along x with ppc the value at x0
+ * (App. C).  method: PIC_MJ_EXACT (inverse CDF of the marginal of p along
+ * beta, Eq. distr_y, then the conditional of Eq. finding_u), PIC_MJ_MLP (the
+ * learned inverse CDF, see pic_mlp_*), PIC_MJ_NAIVE_BOOST (rest-frame
+ * sample boosted particle by particle, Sect. 4.2; wrong for relativistic
+ * theta and beta, kept as a control).  colocate_with >= 0 copies the
+ * positions of that species (pairs on top of each other, rho = 0, Sect. 2.1).
+ * The momenta are then integrated back by -dt/2 (App. A.3.1).  seed selects
+ * the counter-based random stream (Philox-4x32-10). */
+pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double ppc, double theta,
+                                    const double beta[3], int profile, const double *profile_params,
+                                    int method, int colocate_with, uint64_t seed);
+
+/* Advance every run by nsteps steps of the main loop (App. A.3.1).  Queued
+ * on the context stream; unless PIC_FLAG_ASYNC, synchronises and reports a
+ * device-side error flag (PIC_ESTATE when a particle moved more than one cell
+ * in a step, PIC_ETIMEOUT when a bounded wait gave up). */
+pic_status pic_step(pic_ctx *ctx, int nsteps);
+
+/* Wait for queued work and report the device-side error flag. */
+pic_status pic_sync(pic_ctx *ctx);
+
+/* FP64 diagnostics of one run (see pic_diag); synchronises. */
+pic_status pic_diagnostics(pic_ctx *ctx, int run, pic_diag *out);
+
+/* Per-step energy history recorded by the step kernels at no extra pass
+ * (units of p m_e c^2, App. A.2): for each step n taken since the last
+ * pic_set_state or load (at most 65536 steps are recorded, up to max_steps
+ * are returned), out[4n + 0] = kinetic energy at t_n (mean of gamma - 1 over
+ * u^{t-dt/2} and u^{t+dt/2}, all species), out[4n + 1] = electric energy of
+ * e^t, out[4n + 2] = magnetic energy of b^t, out[4n + 3] = their sum.
+ * *nout receives the number of steps written.  Synchronises. */
+pic_status pic_energy_history(pic_ctx *ctx, int run, double *out, int64_t max_steps, int64_t *nout);
+
+/* Tuning actually used by a context: tile shape, sort interval, halo. */
+pic_status pic_get_tuning(const pic_ctx *ctx, int tile[3], int *sort_interval, int *halo);
+
+/* Counters of the last pic_step, for benchmarks: kernel launches queued per
+ * step (all runs, averaged over the call) and algorithmic bytes moved per
+ * particle-step by the push/deposit kernel (particle state read + written). */
+pic_status pic_get_counters(const pic_ctx *ctx, int64_t *launches_per_step, double *bytes_per_particle_step);
+
+/* With PIC_FLAG_TIMING: total device time (ms, CUDA events on the context
+ * stream) and number of launches of one kernel class since the last call to
+ * pic_kernel_time with reset != 0.  Synchronises. */
+pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

@@ -1,0 +1,835 @@
+// capi.cu -- host runtime behind the C ABI of include/pic.h: context and device
+// memory, state transfer, step orchestration, diagnostics.
+//
+// One step of one run (main loop of App. A.3.1), state e^t, b^{t-dt/2}, x^t, u^{t-dt/2}:
+//   [re-sort particles by tile when due]                    (mixed path)
+//   b += -(dt/2) curl e            -> b^t; FP64 sums of e^2, b^2 at t recorded
+//   node fields E, B at t            (mixed path, App. A.3.3 averages)
+//   per species: gather, Boris, move, deposit into J        (steps 2, 3, 8, 9)
+//   b += -(dt/2) curl e            -> b^{t+dt/2}            (steps 4, 5)
+//   e += dt curl b + J, zero the other J buffer             (steps 6, 7, 11, 12)
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+namespace {
+
+struct SpeciesState {
+    double q_over_e = 0, m_over_me = 1, alpha = 0, h = 0;
+    int64_t cap = 0, n = 0;
+    Species64 s64{};            // FP64 path
+    SpeciesMixed mb[2]{};       // mixed path: current and sort target
+    int cur = 0;
+    int *tile_start = nullptr;  // ntiles + 1
+};
+
+struct Run {
+    pic_run_desc d{};
+    Geom g{};
+    TileGeom t{};
+    int sort_interval = 4;
+    int since_sort = 0;
+    bool sorted = false;
+    void *F = nullptr;          // 6 planes of Real (e_x..b_z), padded
+    void *J = nullptr;          // 2 buffers x 3 planes of Real, padded
+    int jcur = 0;
+    float4 *nf = nullptr;       // node fields (mixed)
+    SpeciesState sp[PIC_MAX_SPECIES];
+    int *counts = nullptr, *offsets = nullptr, *block_sums = nullptr;
+    double *rho_s = nullptr, *rho_tot = nullptr, *divb = nullptr;
+    double *acc = nullptr;      // diagnostics accumulators (64 doubles)
+    double *hist = nullptr;     // energy history, 8 doubles per step
+    int64_t hist_cap = 0, hist_n = 0;
+    int64_t step = 0;
+    double inv_alpha_abs = 1;
+};
+
+}  // namespace
+
+struct pic_ctx {
+    int precision = PIC_FP64;
+    uint32_t flags = 0;
+    cudaStream_t stream = nullptr;
+    pic_allocator alloc{};
+    bool have_alloc = false;
+    std::vector<Run> runs;
+    int *d_err = nullptr;
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
+    std::string err;
+    int64_t launches_per_step = 0;
+    double bytes_per_ps = 0;
+    // PIC_FLAG_TIMING: event pairs per kernel class, resolved in pic_kernel_time
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[3];
+    std::vector<cudaEvent_t> ev_pool;
+    double ev_ms[3] = {0, 0, 0};
+    int64_t ev_n[3] = {0, 0, 0};
+};
+
+namespace {
+
+constexpr int64_t kHistCap = 1 << 16;
+
+pic_status fail(pic_ctx *c, pic_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+cudaEvent_t take_event(pic_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Scoped CUDA-event bracket around the kernels of one class (PIC_FLAG_TIMING).
+struct KTimer {
+    pic_ctx *ctx;
+    int cls;
+    cudaEvent_t a = nullptr;
+    KTimer(pic_ctx *c, int k) : ctx(c), cls(k) {
+        if (ctx->flags & PIC_FLAG_TIMING) {
+            a = take_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~KTimer() {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, ctx->stream);
+            ctx->ev_pending[cls].push_back({a, b});
+        }
+    }
+};
+
+void *dev_alloc(pic_ctx *ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (ctx->have_alloc) p = ctx->alloc.alloc(bytes, ctx->alloc.user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) ctx->allocs.push_back({p, bytes});
+    return p;
+}
+
+size_t real_size(const pic_ctx *ctx) { return ctx->precision == PIC_FP64 ? sizeof(double) : sizeof(float); }
+
+template <typename R>
+FieldPtrs<R> fields_of(Run &r) {
+    FieldPtrs<R> f;
+    R *F = (R *)r.F;
+    for (int c = 0; c < 3; ++c) {
+        f.e[c] = F + (size_t)c * r.g.pcells;
+        f.b[c] = F + (size_t)(3 + c) * r.g.pcells;
+    }
+    return f;
+}
+
+template <typename R>
+R *jplane(Run &r, int buf, int c) {
+    return (R *)r.J + ((size_t)buf * 3 + c) * r.g.pcells;
+}
+
+// ------------------------------------------------------------ conversion kernels
+
+template <typename R>
+__global__ void k_pad_field(Geom g, const double *src, R *dst) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(p % g.px);
+        const long long q = p / g.px;
+        const int pj = (int)(q % g.py), pk = (int)(q / g.py);
+        const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
+        dst[p] = (R)src[((long long)k * g.ny + j) * g.nx + i];
+    }
+}
+
+template <typename R>
+__global__ void k_unpad_field(Geom g, const R *src, double *dst) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % g.nx);
+        const long long r = q / g.nx;
+        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        dst[q] = (double)src[g.pidx(i, j, k)];
+    }
+}
+
+// staging: 6 planes of m doubles (x, y, z, ux, uy, uz) for ids [a, a+m)
+__global__ void k_upload_mixed(Geom g, const double *st, long long m, long long a, SpeciesMixed d, int *err) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        int c[3] = {0, 0, 0};
+        float o[3] = {0.f, 0.f, 0.f};
+        const int n3[3] = {g.nx, g.ny, g.nz};
+        for (int ax = 0; ax < g.ndim; ++ax) {
+            const double x = st[ax * m + q];
+            double f = floor(x);
+            int ci = (int)f;
+            float off = (float)(x - f);
+            if (off >= 1.0f) { off = 0.0f; ci += 1; }
+            if (g.bcx == 1 && ax == 0 && ci >= g.nx) { ci = g.nx - 1; off = 1.0f; }
+            else if (ci >= n3[ax]) ci -= n3[ax];
+            if (ci < 0 || ci >= n3[ax]) atomicOr(err, ERR_NONFINITE);
+            c[ax] = ci;
+            o[ax] = off;
+        }
+        d.cell[a + q] = pack_cell(g.ndim, c[0], c[1], c[2]);
+        d.off[0][a + q] = o[0];
+        d.off[1][a + q] = o[1];
+        if (g.ndim == 3) d.off[2][a + q] = o[2];
+        d.u[0][a + q] = (float)st[3 * m + q];
+        d.u[1][a + q] = (float)st[4 * m + q];
+        d.u[2][a + q] = (float)st[5 * m + q];
+        d.id[a + q] = (int32_t)(a + q);
+    }
+}
+
+__global__ void k_download_mixed(Geom g, SpeciesMixed s, long long n, long long a, long long m, double *st) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const long long id = s.id[p];
+        if (id < a || id >= a + m) continue;
+        const long long q = id - a;
+        int i, j, k;
+        unpack_cell(g.ndim, s.cell[p], i, j, k);
+        st[q] = (double)i + (double)s.off[0][p];
+        st[m + q] = (double)j + (double)s.off[1][p];
+        st[2 * m + q] = g.ndim == 3 ? (double)k + (double)s.off[2][p] : 0.0;
+        st[3 * m + q] = s.u[0][p];
+        st[4 * m + q] = s.u[1][p];
+        st[5 * m + q] = s.u[2][p];
+    }
+}
+
+inline int nblk(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+// ------------------------------------------------------------ validation
+
+bool validate(const pic_run_desc &d, int precision, std::string &why) {
+    char b[256];
+    if (d.ndim != 2 && d.ndim != 3) { why = "ndim must be 2 or 3"; return false; }
+    if (d.ndim == 2 && d.nz != 1) { why = "nz must be 1 when ndim = 2"; return false; }
+    const int lim = d.ndim == 2 ? 65535 : 2047;
+    if (d.nx < 2 || d.ny < 2 || (d.ndim == 3 && d.nz < 2) || d.nx > lim || d.ny > lim || d.nz > lim) {
+        snprintf(b, sizeof b, "grid %dx%dx%d outside 2..%d per axis", d.nx, d.ny, d.nz, lim);
+        why = b;
+        return false;
+    }
+    if (!(d.dt > 0) || !(d.dt < 1.0 / std::sqrt((double)d.ndim))) {
+        snprintf(b, sizeof b, "dt = %g violates the Courant limit dt < 1/sqrt(%d)", d.dt, d.ndim);
+        why = b;
+        return false;
+    }
+    if (!(d.n_x > 0) || !(d.rho_sp0 > 0) || !std::isfinite(d.n_x) || !std::isfinite(d.rho_sp0)) {
+        why = "n_x and rho_sp0 must be positive";
+        return false;
+    }
+    if (d.nspecies < 1 || d.nspecies > PIC_MAX_SPECIES) { why = "nspecies must be 1..4"; return false; }
+    for (int s = 0; s < d.nspecies; ++s) {
+        const pic_species_desc &sp = d.species[s];
+        if (!(sp.q_over_e != 0) || !(sp.m_over_me > 0) || sp.capacity < 0 || sp.capacity > (int64_t)INT32_MAX) {
+            snprintf(b, sizeof b, "species %d: q/e must be non-zero, m/m_e positive, capacity 0..2^31-1", s);
+            why = b;
+            return false;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (d.bc[a] != PIC_BC_PERIODIC && d.bc[a] != PIC_BC_CONDUCTOR) { why = "unknown boundary kind"; return false; }
+        if (a > 0 && d.bc[a] != PIC_BC_PERIODIC) { why = "conducting walls are supported along x only"; return false; }
+    }
+    if (d.bc[0] == PIC_BC_CONDUCTOR && precision == PIC_MIXED) {
+        why = "conducting walls are available in the FP64 path only";
+        return false;
+    }
+    return true;
+}
+
+void choose_tiles(Run &r, const pic_opts *o) {
+    const pic_run_desc &d = r.d;
+    int T[3], H;
+    if (d.ndim == 2) { T[0] = 16; T[1] = 16; T[2] = 1; H = 4; }
+    else { T[0] = 8; T[1] = 8; T[2] = 8; H = 3; }
+    if (o) {
+        for (int a = 0; a < 3; ++a)
+            if (o->tile[a] > 0) T[a] = o->tile[a];
+    }
+    const int n3[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < d.ndim; ++a) T[a] = std::max(1, std::min(T[a], n3[a]));
+    if (d.ndim == 2) T[2] = 1;
+    int hmax = std::min(d.nx, d.ny);
+    if (d.ndim == 3) hmax = std::min(hmax, d.nz);
+    H = std::max(1, std::min(H, hmax));
+    r.t.H = H;
+    for (int a = 0; a < 3; ++a) {
+        r.t.T[a] = T[a];
+        r.t.R[a] = (a < d.ndim) ? T[a] + 2 * H : 1;
+        r.t.ntile[a] = (a < d.ndim) ? (n3[a] + T[a] - 1) / T[a] : 1;
+    }
+    r.t.ntiles = r.t.ntile[0] * r.t.ntile[1] * r.t.ntile[2];
+    r.t.cells_per_tile = T[0] * T[1] * T[2];
+    r.sort_interval = (o && o->sort_interval > 0) ? o->sort_interval : (d.ndim == 2 ? 4 : 2);
+}
+
+pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
+    const pic_run_desc &d = r.d;
+    const bool mixed = ctx->precision == PIC_MIXED;
+    if (mixed) choose_tiles(r, o);
+    const int G = mixed ? r.t.H : 0;
+    Geom &g = r.g;
+    g.ndim = d.ndim; g.nx = d.nx; g.ny = d.ny; g.nz = d.ndim == 2 ? 1 : d.nz;
+    g.G = G; g.Gz = d.ndim == 3 ? G : 0;
+    g.px = g.nx + 2 * G; g.py = g.ny + 2 * G; g.pz = g.nz + 2 * g.Gz;
+    g.pcells = (long long)g.px * g.py * g.pz;
+    g.bcx = d.bc[0];
+    r.inv_alpha_abs = d.n_x * d.n_x * d.rho_sp0 / 2.0;
+    const size_t rs = real_size(ctx);
+    const long long ncell = (long long)g.nx * g.ny * g.nz;
+    r.F = dev_alloc(ctx, 6 * rs * g.pcells);
+    r.J = dev_alloc(ctx, 6 * rs * g.pcells);
+    if (!r.F || !r.J) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the field arrays");
+    CK(cudaMemsetAsync(r.F, 0, 6 * rs * g.pcells, ctx->stream));
+    CK(cudaMemsetAsync(r.J, 0, 6 * rs * g.pcells, ctx->stream));
+    if (mixed) {
+        r.nf = (float4 *)dev_alloc(ctx, 2 * sizeof(float4) * g.pcells);
+        const long long nkeys = (long long)r.t.ntiles * r.t.cells_per_tile;
+        r.counts = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
+        r.offsets = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
+        r.block_sums = (int *)dev_alloc(ctx, sizeof(int) * sort_scan_scratch(nkeys));
+        if (!r.nf || !r.counts || !r.offsets || !r.block_sums)
+            return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the tile buffers");
+    }
+    r.rho_s = (double *)dev_alloc(ctx, sizeof(double) * ncell);
+    r.rho_tot = (double *)dev_alloc(ctx, sizeof(double) * ncell);
+    r.divb = (double *)dev_alloc(ctx, sizeof(double) * ncell);
+    r.acc = (double *)dev_alloc(ctx, sizeof(double) * 64);
+    r.hist_cap = kHistCap;
+    r.hist = (double *)dev_alloc(ctx, sizeof(double) * 8 * r.hist_cap);
+    if (!r.rho_s || !r.rho_tot || !r.divb || !r.acc || !r.hist)
+        return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the diagnostics buffers");
+    CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, ctx->stream));
+    for (int s = 0; s < d.nspecies; ++s) {
+        SpeciesState &S = r.sp[s];
+        S.q_over_e = d.species[s].q_over_e;
+        S.m_over_me = d.species[s].m_over_me;
+        S.alpha = 2.0 * (S.q_over_e > 0 ? 1.0 : -1.0) / (d.n_x * d.n_x * d.rho_sp0);
+        S.h = S.q_over_e / S.m_over_me;
+        S.cap = d.species[s].capacity;
+        S.n = 0;
+        const size_t cap = (size_t)std::max<int64_t>(S.cap, 1);
+        if (!mixed) {
+            for (int a = 0; a < 3; ++a) {
+                S.s64.x[a] = (double *)dev_alloc(ctx, sizeof(double) * cap);
+                S.s64.u[a] = (double *)dev_alloc(ctx, sizeof(double) * cap);
+                if (!S.s64.x[a] || !S.s64.u[a]) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for particles");
+            }
+        } else {
+            for (int b = 0; b < 2; ++b) {
+                SpeciesMixed &m = S.mb[b];
+                m.cell = (uint32_t *)dev_alloc(ctx, sizeof(uint32_t) * cap);
+                m.id = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * cap);
+                for (int a = 0; a < 3; ++a) {
+                    m.off[a] = (a < d.ndim) ? (float *)dev_alloc(ctx, sizeof(float) * cap) : nullptr;
+                    m.u[a] = (float *)dev_alloc(ctx, sizeof(float) * cap);
+                    if ((a < d.ndim && !m.off[a]) || !m.u[a]) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for particles");
+                }
+                if (!m.cell || !m.id) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for particles");
+            }
+            S.tile_start = (int *)dev_alloc(ctx, sizeof(int) * (r.t.ntiles + 1));
+            if (!S.tile_start) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for tile offsets");
+            CK(cudaMemsetAsync(S.tile_start, 0, sizeof(int) * (r.t.ntiles + 1), ctx->stream));
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status check_run(pic_ctx *ctx, int run) {
+    if (!ctx) return PIC_EINVAL;
+    if (run < 0 || run >= (int)ctx->runs.size()) return fail(ctx, PIC_EINVAL, "run index %d out of range", run);
+    return PIC_OK;
+}
+
+pic_status read_err(pic_ctx *ctx) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (e) {
+        CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+        if (e & ERR_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "a bounded device wait gave up");
+        if (e & ERR_FAST_MOVE) return fail(ctx, PIC_ESTATE, "a particle moved more than one cell in one step");
+        if (e & ERR_SORT) return fail(ctx, PIC_ESTATE, "particle cell outside the grid during sort");
+        if (e & ERR_NONFINITE) return fail(ctx, PIC_ENUMERIC, "non-finite or out-of-domain particle coordinate");
+    }
+    return PIC_OK;
+}
+
+// ------------------------------------------------------------ stepping
+
+void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
+    SortArgs a;
+    a.g = r.g;
+    a.t = r.t;
+    a.n = S.n;
+    a.src = S.mb[S.cur];
+    a.dst = S.mb[1 - S.cur];
+    a.counts = r.counts;
+    a.offsets = r.offsets;
+    a.block_sums = r.block_sums;
+    a.tile_start = S.tile_start;
+    a.err = ctx->d_err;
+    launch_sort(a, ctx->stream);
+    S.cur = 1 - S.cur;
+}
+
+void step_run(pic_ctx *ctx, Run &r) {
+    cudaStream_t s = ctx->stream;
+    double *hslot = (r.hist_n < r.hist_cap) ? r.hist + 8 * r.hist_n : nullptr;
+    const int nsp = r.d.nspecies;
+    if (ctx->precision == PIC_FP64) {
+        FieldPtrs<double> f = fields_of<double>(r);
+        {
+            KTimer t(ctx, PIC_KERNEL_FIELD);
+            launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, hslot ? hslot + 2 : nullptr, s);
+        }
+        double *J[3] = {jplane<double>(r, r.jcur, 0), jplane<double>(r, r.jcur, 1), jplane<double>(r, r.jcur, 2)};
+        {
+            KTimer t(ctx, PIC_KERNEL_PUSH);
+            for (int q = 0; q < nsp; ++q) {
+                SpeciesState &S = r.sp[q];
+                launch_push_fp64(r.g, f, J, S.s64, S.n, S.h, S.alpha, r.d.dt, 0, S.m_over_me, hslot, ctx->d_err, s);
+            }
+        }
+        double *Z[3] = {jplane<double>(r, 1 - r.jcur, 0), jplane<double>(r, 1 - r.jcur, 1),
+                        jplane<double>(r, 1 - r.jcur, 2)};
+        const double *Jc[3] = {J[0], J[1], J[2]};
+        {
+            KTimer t(ctx, PIC_KERNEL_FIELD);
+            launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, nullptr, s);
+            launch_e_advance<double>(r.g, f, Jc, Z, r.d.dt, s);
+        }
+        ctx->bytes_per_ps = r.d.ndim == 2 ? 80.0 : 96.0;
+        ctx->launches_per_step = 3 + nsp;
+    } else {
+        int launches = 0;
+        if (!r.sorted || r.since_sort >= r.sort_interval) {
+            KTimer t(ctx, PIC_KERNEL_SORT);
+            for (int q = 0; q < nsp; ++q) sort_species(ctx, r, r.sp[q]);
+            r.sorted = true;
+            r.since_sort = 0;
+            launches += 6 * nsp;
+        }
+        FieldPtrs<float> f = fields_of<float>(r);
+        {
+            KTimer t(ctx, PIC_KERNEL_FIELD);
+            launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, hslot ? hslot + 2 : nullptr, s);
+            launch_node_fields(r.g, f, r.nf, s);
+        }
+        float *J[3] = {jplane<float>(r, r.jcur, 0), jplane<float>(r, r.jcur, 1), jplane<float>(r, r.jcur, 2)};
+        KTimer* tp = new KTimer(ctx, PIC_KERNEL_PUSH);
+        for (int q = 0; q < nsp; ++q) {
+            SpeciesState &S = r.sp[q];
+            MixedStepArgs a;
+            a.g = r.g;
+            a.t = r.t;
+            a.nf = r.nf;
+            for (int c = 0; c < 3; ++c) a.J[c] = J[c];
+            a.sp = S.mb[S.cur];
+            a.tile_start = S.tile_start;
+            a.h = (float)S.h;
+            a.alpha = (float)S.alpha;
+            a.dt = (float)r.d.dt;
+            a.mode = 0;
+            a.kin_acc = hslot;
+            a.m_over_me = S.m_over_me;
+            a.err = ctx->d_err;
+            launch_push_mixed(a, s);
+        }
+        delete tp;
+        float *Z[3] = {jplane<float>(r, 1 - r.jcur, 0), jplane<float>(r, 1 - r.jcur, 1), jplane<float>(r, 1 - r.jcur, 2)};
+        const float *Jc[3] = {J[0], J[1], J[2]};
+        {
+            KTimer t(ctx, PIC_KERNEL_FIELD);
+            launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, nullptr, s);
+            launch_e_advance<float>(r.g, f, Jc, Z, (float)r.d.dt, s);
+        }
+        r.since_sort++;
+        launches += 4 + nsp;
+        ctx->launches_per_step = launches;
+        ctx->bytes_per_ps = r.d.ndim == 2 ? 48.0 : 56.0;
+    }
+    r.jcur = 1 - r.jcur;
+    r.step++;
+    if (r.hist_n < r.hist_cap) r.hist_n++;
+}
+
+}  // namespace
+
+// ================================================================== ABI
+
+extern "C" {
+
+int pic_abi_version(void) { return PIC_ABI_VERSION; }
+
+pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, pic_ctx **out) {
+    if (!out) return PIC_EINVAL;
+    *out = nullptr;
+    if (!runs || nruns < 1) return PIC_EINVAL;
+    const int precision = opts ? opts->precision : PIC_FP64;
+    if (precision != PIC_FP64 && precision != PIC_MIXED) return PIC_EINVAL;
+    for (int r = 0; r < nruns; ++r) {
+        std::string why;
+        if (!validate(runs[r], precision, why)) return PIC_EINVAL;
+    }
+    if (opts && opts->allocator && (!opts->allocator->alloc || !opts->allocator->free)) return PIC_EINVAL;
+    if (opts && (opts->sort_interval < 0 || opts->tile[0] < 0 || opts->tile[1] < 0 || opts->tile[2] < 0))
+        return PIC_EINVAL;
+    pic_ctx *ctx = new pic_ctx();
+    ctx->precision = precision;
+    ctx->flags = opts ? opts->flags : 0;
+    ctx->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+    if (opts && opts->allocator) { ctx->alloc = *opts->allocator; ctx->have_alloc = true; }
+    ctx->runs.resize(nruns);
+    ctx->d_err = (int *)dev_alloc(ctx, sizeof(int));
+    if (!ctx->d_err) { pic_destroy(ctx); return PIC_ENOMEM; }
+    if (cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream) != cudaSuccess) { pic_destroy(ctx); return PIC_ECUDA; }
+    size_t stage = 0;
+    for (int r = 0; r < nruns; ++r) {
+        ctx->runs[r].d = runs[r];
+        pic_status st = setup_run(ctx, ctx->runs[r], opts);
+        if (st != PIC_OK) { pic_destroy(ctx); return st; }
+        const Geom &g = ctx->runs[r].g;
+        stage = std::max(stage, sizeof(double) * (size_t)g.nx * g.ny * g.nz);
+        int64_t cap = 0;
+        for (int s = 0; s < runs[r].nspecies; ++s) cap = std::max<int64_t>(cap, runs[r].species[s].capacity);
+        stage = std::max(stage, 6 * sizeof(double) * (size_t)std::min<int64_t>(cap, 1 << 24));
+    }
+    ctx->staging_bytes = stage;
+    ctx->staging = dev_alloc(ctx, stage);
+    if (!ctx->staging) { pic_destroy(ctx); return PIC_ENOMEM; }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { pic_destroy(ctx); return PIC_ECUDA; }
+    *out = ctx;
+    return PIC_OK;
+}
+
+void pic_destroy(pic_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < 3; ++k)
+        for (auto &pr : ctx->ev_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    for (auto &a : ctx->allocs) {
+        if (ctx->have_alloc) ctx->alloc.free(a.first, a.second, ctx->alloc.user);
+        else cudaFree(a.first);
+    }
+    delete ctx;
+}
+
+const char *pic_last_error(const pic_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    if (!in || !in->fields) return fail(ctx, PIC_EINVAL, "null state view or field buffer");
+    Run &r = ctx->runs[run];
+    const Geom &g = r.g;
+    const long long ncell = (long long)g.nx * g.ny * g.nz;
+    // host-side validation before any device work
+    for (long long q = 0; q < 6 * ncell; ++q)
+        if (!std::isfinite(in->fields[q])) return fail(ctx, PIC_ENUMERIC, "non-finite field value at %lld", q);
+    const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+    for (int s = 0; s < r.d.nspecies; ++s) {
+        const int64_t n = in->count[s];
+        if (n < 0 || n > r.sp[s].cap) return fail(ctx, PIC_EINVAL, "species %d: count %lld exceeds capacity", s, (long long)n);
+        if (n > 0 && !in->particles[s]) return fail(ctx, PIC_EINVAL, "species %d: null particle buffer", s);
+        const double *P = in->particles[s];
+        for (int a = 0; a < 6; ++a) {
+            if (a == 2 && g.ndim == 2) continue;
+            for (int64_t p = 0; p < n; ++p) {
+                const double v = P[a * n + p];
+                if (!std::isfinite(v)) return fail(ctx, PIC_ENUMERIC, "species %d: non-finite value", s);
+                if (a < 3) {
+                    const bool ok = (a == 0 && g.bcx == 1) ? (v >= 0.0 && v <= L[0]) : (v >= 0.0 && v < L[a]);
+                    if (!ok) return fail(ctx, PIC_EINVAL, "species %d: position %g outside the domain on axis %d", s, v, a);
+                }
+            }
+        }
+    }
+    cudaStream_t sm = ctx->stream;
+    double *stg = (double *)ctx->staging;
+    const size_t rs = real_size(ctx);
+    for (int c = 0; c < 6; ++c) {
+        CK(cudaMemcpyAsync(stg, in->fields + c * ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, sm));
+        if (ctx->precision == PIC_FP64)
+            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (double *)r.F + c * g.pcells);
+        else
+            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (float *)r.F + c * g.pcells);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemsetAsync(r.J, 0, 6 * rs * g.pcells, sm));
+    r.jcur = 0;
+    for (int s = 0; s < r.d.nspecies; ++s) {
+        SpeciesState &S = r.sp[s];
+        const int64_t n = in->count[s];
+        S.n = n;
+        const double *P = in->particles[s];
+        if (ctx->precision == PIC_FP64) {
+            for (int a = 0; a < 3; ++a) {
+                if (n == 0) break;
+                if (a < g.ndim) CK(cudaMemcpyAsync(S.s64.x[a], P + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, sm));
+                else CK(cudaMemsetAsync(S.s64.x[a], 0, sizeof(double) * n, sm));
+                CK(cudaMemcpyAsync(S.s64.u[a], P + (3 + a) * n, sizeof(double) * n, cudaMemcpyHostToDevice, sm));
+            }
+        } else {
+            S.cur = 0;
+            const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
+            for (int64_t a0 = 0; a0 < n; a0 += chunk) {
+                const int64_t m = std::min(chunk, n - a0);
+                for (int a = 0; a < 6; ++a) {
+                    if (a == 2 && g.ndim == 2) continue;
+                    CK(cudaMemcpyAsync(stg + a * m, P + a * n + a0, sizeof(double) * m, cudaMemcpyHostToDevice, sm));
+                }
+                k_upload_mixed<<<nblk(m), 256, 0, sm>>>(g, stg, m, a0, S.mb[0], ctx->d_err);
+                CK(cudaGetLastError());
+            }
+        }
+    }
+    r.sorted = false;
+    r.since_sort = 0;
+    r.step = 0;
+    r.hist_n = 0;
+    CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, sm));
+    return read_err(ctx);
+}
+
+pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    if (!out || !out->fields) return fail(ctx, PIC_EINVAL, "null state view or field buffer");
+    Run &r = ctx->runs[run];
+    const Geom &g = r.g;
+    const long long ncell = (long long)g.nx * g.ny * g.nz;
+    for (int s = 0; s < r.d.nspecies; ++s) {
+        if (out->count[s] < r.sp[s].n)
+            return fail(ctx, PIC_EINVAL, "species %d: buffer holds %lld particles, %lld needed", s,
+                        (long long)out->count[s], (long long)r.sp[s].n);
+        if (r.sp[s].n > 0 && !out->particles[s]) return fail(ctx, PIC_EINVAL, "species %d: null particle buffer", s);
+    }
+    cudaStream_t sm = ctx->stream;
+    double *stg = (double *)ctx->staging;
+    for (int c = 0; c < 6; ++c) {
+        if (ctx->precision == PIC_FP64)
+            k_unpad_field<double><<<nblk(ncell), 256, 0, sm>>>(g, (double *)r.F + c * g.pcells, stg);
+        else
+            k_unpad_field<float><<<nblk(ncell), 256, 0, sm>>>(g, (float *)r.F + c * g.pcells, stg);
+        CK(cudaMemcpyAsync(out->fields + c * ncell, stg, sizeof(double) * ncell, cudaMemcpyDeviceToHost, sm));
+    }
+    for (int s = 0; s < r.d.nspecies; ++s) {
+        SpeciesState &S = r.sp[s];
+        const int64_t n = S.n;
+        out->count[s] = n;
+        double *P = out->particles[s];
+        if (n == 0) continue;
+        if (ctx->precision == PIC_FP64) {
+            for (int a = 0; a < 3; ++a) {
+                if (a < g.ndim) CK(cudaMemcpyAsync(P + a * n, S.s64.x[a], sizeof(double) * n, cudaMemcpyDeviceToHost, sm));
+                CK(cudaMemcpyAsync(P + (3 + a) * n, S.s64.u[a], sizeof(double) * n, cudaMemcpyDeviceToHost, sm));
+            }
+            if (g.ndim == 2) std::memset(P + 2 * n, 0, sizeof(double) * n);
+        } else {
+            const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
+            for (int64_t a0 = 0; a0 < n; a0 += chunk) {
+                const int64_t m = std::min(chunk, n - a0);
+                k_download_mixed<<<nblk(n), 256, 0, sm>>>(g, S.mb[S.cur], n, a0, m, stg);
+                CK(cudaGetLastError());
+                for (int a = 0; a < 6; ++a)
+                    CK(cudaMemcpyAsync(P + a * n + a0, stg + a * m, sizeof(double) * m, cudaMemcpyDeviceToHost, sm));
+            }
+        }
+    }
+    out->step = r.step;
+    CK(cudaStreamSynchronize(sm));
+    return PIC_OK;
+}
+
+pic_status pic_set_uniform_field(pic_ctx *ctx, int run, const double e0[3], const double b0[3]) {
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    if (!e0 || !b0) return fail(ctx, PIC_EINVAL, "null field vector");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(e0[a]) || !std::isfinite(b0[a])) return fail(ctx, PIC_ENUMERIC, "non-finite field vector");
+    Run &r = ctx->runs[run];
+    if (ctx->precision == PIC_FP64) launch_add_uniform<double>(r.g, fields_of<double>(r), e0, b0, ctx->stream);
+    else launch_add_uniform<float>(r.g, fields_of<float>(r), e0, b0, ctx->stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx *ctx, int nsteps) {
+    if (!ctx) return PIC_EINVAL;
+    if (nsteps < 0) return fail(ctx, PIC_EINVAL, "nsteps must be >= 0");
+    for (int n = 0; n < nsteps; ++n)
+        for (auto &r : ctx->runs) step_run(ctx, r);
+    CK(cudaGetLastError());
+    if (ctx->flags & PIC_FLAG_ASYNC) return PIC_OK;
+    return read_err(ctx);
+}
+
+pic_status pic_sync(pic_ctx *ctx) {
+    if (!ctx) return PIC_EINVAL;
+    CK(cudaGetLastError());
+    return read_err(ctx);
+}
+
+pic_status pic_diagnostics(pic_ctx *ctx, int run, pic_diag *out) {
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    if (!out) return fail(ctx, PIC_EINVAL, "null output");
+    Run &r = ctx->runs[run];
+    const Geom &g = r.g;
+    cudaStream_t sm = ctx->stream;
+    const long long ncell = (long long)g.nx * g.ny * g.nz;
+    const int nsp = r.d.nspecies;
+    // acc layout: [0..5] field sums, [6 + 6 s ..] particle sums of species s,
+    // [40] nonfinite (as long long), [41 + s] max |rho_s|, [48] gauss max
+    CK(cudaMemsetAsync(r.acc, 0, sizeof(double) * 64, sm));
+    long long *nonfinite = reinterpret_cast<long long *>(r.acc + 40);
+    if (ctx->precision == PIC_FP64) launch_field_diag<double>(g, fields_of<double>(r), r.acc, nonfinite, sm);
+    else launch_field_diag<float>(g, fields_of<float>(r), r.acc, nonfinite, sm);
+    CK(cudaMemsetAsync(r.rho_tot, 0, sizeof(double) * ncell, sm));
+    for (int s = 0; s < nsp; ++s) {
+        SpeciesState &S = r.sp[s];
+        CK(cudaMemsetAsync(r.rho_s, 0, sizeof(double) * ncell, sm));
+        if (ctx->precision == PIC_FP64) {
+            launch_particle_diag64(g, S.s64, S.n, S.m_over_me, r.acc + 6 + 6 * s, nonfinite, sm);
+            launch_rho64(g, S.s64, S.n, S.alpha, r.rho_s, sm);
+            launch_rho64(g, S.s64, S.n, S.alpha, r.rho_tot, sm);
+        } else {
+            launch_particle_diag_mixed(g, S.mb[S.cur], S.n, S.m_over_me, r.acc + 6 + 6 * s, nonfinite, sm);
+            launch_rho_mixed(g, S.mb[S.cur], S.n, S.alpha, r.rho_s, sm);
+            launch_rho_mixed(g, S.mb[S.cur], S.n, S.alpha, r.rho_tot, sm);
+        }
+        launch_max_abs_diff(r.rho_s, nullptr, ncell, r.acc + 41 + s, sm);
+    }
+    if (ctx->precision == PIC_FP64) launch_div_e<double>(g, fields_of<double>(r), r.divb, sm);
+    else launch_div_e<float>(g, fields_of<float>(r), r.divb, sm);
+    launch_max_abs_diff(r.divb, r.rho_tot, ncell, r.acc + 48, sm);
+    CK(cudaGetLastError());
+    double h[64];
+    CK(cudaMemcpyAsync(h, r.acc, sizeof h, cudaMemcpyDeviceToHost, sm));
+    CK(cudaStreamSynchronize(sm));
+    std::memset(out, 0, sizeof *out);
+    out->step = r.step;
+    out->nspecies = nsp;
+    for (int c = 0; c < 3; ++c) {
+        out->field_e[c] = 0.5 * h[c] * r.inv_alpha_abs;
+        out->field_b[c] = 0.5 * h[3 + c] * r.inv_alpha_abs;
+    }
+    out->rho_max = 0;
+    for (int s = 0; s < nsp; ++s) {
+        const double *v = h + 6 + 6 * s;
+        out->count[s] = r.sp[s].n;
+        out->kinetic[s] = r.sp[s].m_over_me * v[0];
+        for (int c = 0; c < 3; ++c) out->sum_u[s][c] = v[1 + c];
+        out->temperature[s] = r.sp[s].n > 0 ? v[4] / (3.0 * (double)r.sp[s].n) : 0.0;
+        out->rho_max = std::max(out->rho_max, h[41 + s]);
+    }
+    out->gauss_max = h[48];
+    std::memcpy(&out->nonfinite, &h[40], sizeof(long long));
+    return out->nonfinite ? fail(ctx, PIC_ENUMERIC, "%lld non-finite values", (long long)out->nonfinite) : PIC_OK;
+}
+
+pic_status pic_energy_history(pic_ctx *ctx, int run, double *out, int64_t max_steps, int64_t *nout) {
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    if (!nout || (max_steps > 0 && !out)) return fail(ctx, PIC_EINVAL, "null output");
+    Run &r = ctx->runs[run];
+    const int64_t n = std::min<int64_t>(r.hist_n, std::max<int64_t>(max_steps, 0));
+    std::vector<double> h(8 * std::max<int64_t>(n, 1));
+    if (n > 0) CK(cudaMemcpyAsync(h.data(), r.hist, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t q = 0; q < n; ++q) {
+        const double *v = &h[8 * q];
+        out[4 * q + 0] = 0.5 * (v[0] + v[1]);
+        out[4 * q + 1] = 0.5 * (v[2] + v[3] + v[4]) * r.inv_alpha_abs;
+        out[4 * q + 2] = 0.5 * (v[5] + v[6] + v[7]) * r.inv_alpha_abs;
+        out[4 * q + 3] = out[4 * q + 0] + out[4 * q + 1] + out[4 * q + 2];
+    }
+    *nout = n;
+    return PIC_OK;
+}
+
+pic_status pic_get_tuning(const pic_ctx *ctx, int tile[3], int *sort_interval, int *halo) {
+    if (!ctx || ctx->runs.empty()) return PIC_EINVAL;
+    const Run &r = ctx->runs[0];
+    if (tile) for (int a = 0; a < 3; ++a) tile[a] = r.t.T[a];
+    if (sort_interval) *sort_interval = r.sort_interval;
+    if (halo) *halo = r.t.H;
+    return PIC_OK;
+}
+
+pic_status pic_get_counters(const pic_ctx *ctx, int64_t *launches_per_step, double *bytes_per_particle_step) {
+    if (!ctx) return PIC_EINVAL;
+    if (launches_per_step) *launches_per_step = ctx->launches_per_step;
+    if (bytes_per_particle_step) *bytes_per_particle_step = ctx->bytes_per_ps;
+    return PIC_OK;
+}
+
+pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *total_ms, int64_t *launches) {
+    if (!ctx) return PIC_EINVAL;
+    if (kernel_class < 0 || kernel_class > 2) return fail(ctx, PIC_EINVAL, "unknown kernel class");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 3; ++k) {
+        for (auto &pr : ctx->ev_pending[k]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) ctx->ev_ms[k] += ms;
+            ctx->ev_n[k]++;
+            ctx->ev_pool.push_back(pr.first);
+            ctx->ev_pool.push_back(pr.second);
+        }
+        ctx->ev_pending[k].clear();
+    }
+    if (total_ms) *total_ms = ctx->ev_ms[kernel_class];
+    if (launches) *launches = ctx->ev_n[kernel_class];
+    if (reset) {
+        for (int k = 0; k < 3; ++k) { ctx->ev_ms[k] = 0; ctx->ev_n[k] = 0; }
+    }
+    return PIC_OK;
+}
+
+pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double ppc, double theta, const double beta[3],
+                                    int profile, const double *profile_params, int method, int colocate_with,
+                                    uint64_t seed) {
+    (void)species; (void)ppc; (void)theta; (void)beta; (void)profile; (void)profile_params; (void)method;
+    (void)colocate_with; (void)seed;
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    return fail(ctx, PIC_ESTATE, "the Maxwell-Juttner loader is not built in this library version");
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// fields.cu -- Yee FDTD field kernels (App. A.3.2) and the node-averaged fields
+// used by the gather (App. A.3.3).
+//
+// Every kernel runs one thread per padded cell, ghosts included.  A thread
+// computes the update of its cell from the interior images of the
+// neighbours, so a ghost cell receives exactly the value of the interior cell
+// it mirrors and the padded arrays stay periodic without a separate copy.
+// Each thread reads its own cell and neighbours, and writes only its own cell,
+// of arrays that are not read at neighbour positions in the same kernel, so
+// no two threads race.
+//
+// Roofline: HBM bound.  Algorithmic bytes per cell: b advance 6 reads +
+// 3 writes; e advance 6 + 3 (J) reads, 3 writes, 3 zero-writes; node fields 6
+// reads + 8 writes, in units of sizeof(Real) (float4 pairs for node fields).
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+__device__ inline void padded_coords(const Geom &g, long long p, int &pi, int &pj, int &pk) {
+    pi = (int)(p % g.px);
+    long long q = p / g.px;
+    pj = (int)(q % g.py);
+    pk = (int)(q / g.py);
+}
+
+template <typename R>
+__device__ inline R ld(const R *a, long long i) { return __ldg(a + i); }
+
+// Block-wide FP64 sum of NV values, one atomicAdd per value per block.
+template <int NV>
+__device__ inline void block_accumulate(double (&v)[NV], double *acc) {
+    __shared__ double red[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[q][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = lane < nw ? red[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) atomicAdd(acc + q, x);
+        }
+    }
+}
+
+// b <- b - h curl e (Faraday, Eq. dyn3 on the Yee lattice).  When energy_acc
+// is given, the interior sums of e^2 and b^2 (after the update) are added to
+// energy_acc[0..5] in FP64.
+template <typename R>
+__global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, double *energy_acc) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+        int pi, pj, pk;
+        padded_coords(g, p, pi, pj, pk);
+        const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
+        const long long c = g.pidx(i, j, k);
+        const R ex = ld(f.e[0], c), ey = ld(f.e[1], c), ez = ld(f.e[2], c);
+        const R curl_x = (ld(f.e[2], g.widx(i, j + 1, k)) - ez) - (ld(f.e[1], g.widx(i, j, k + 1)) - ey);
+        const R curl_y = (ld(f.e[0], g.widx(i, j, k + 1)) - ex) - (ld(f.e[2], g.widx(i + 1, j, k)) - ez);
+        const R curl_z = (ld(f.e[1], g.widx(i + 1, j, k)) - ey) - (ld(f.e[0], g.widx(i, j + 1, k)) - ex);
+        R bx = f.b[0][p] - h * curl_x;
+        R by = f.b[1][p] - h * curl_y;
+        R bz = f.b[2][p] - h * curl_z;
+        if (g.bcx == 1 && i == 0) bx = R(0);   // normal b vanishes on the conductor wall (App. A.4)
+        f.b[0][p] = bx;
+        f.b[1][p] = by;
+        f.b[2][p] = bz;
+        if (energy_acc && pi == i + g.G && pj == j + g.G && pk == k + g.Gz) {
+            acc[0] += (double)ex * (double)ex;
+            acc[1] += (double)ey * (double)ey;
+            acc[2] += (double)ez * (double)ez;
+            acc[3] += (double)bx * (double)bx;
+            acc[4] += (double)by * (double)by;
+            acc[5] += (double)bz * (double)bz;
+        }
+    }
+    if (energy_acc) block_accumulate<6>(acc, energy_acc);
+}
+
+// Sum of the current over every padded image of interior cell (i,j,k).
+template <typename R>
+__device__ inline R folded_current(const Geom &g, const R *J, int i, int j, int k) {
+    R s = R(0);
+    const int zlo = g.ndim == 3 ? -1 : 0, zhi = g.ndim == 3 ? 1 : 0;
+    for (int mz = zlo; mz <= zhi; ++mz) {
+        const int qk = k + g.Gz + mz * g.nz;
+        if (qk < 0 || qk >= g.pz) continue;
+        for (int my = -1; my <= 1; ++my) {
+            const int qj = j + g.G + my * g.ny;
+            if (qj < 0 || qj >= g.py) continue;
+            for (int mx = -1; mx <= 1; ++mx) {
+                const int qi = i + g.G + mx * g.nx;
+                if (qi < 0 || qi >= g.px) continue;
+                s += J[((long long)qk * g.py + qj) * g.px + qi];
+            }
+        }
+    }
+    return s;
+}
+
+// e <- e + dt curl b + J (Ampere, Eq. dyn4 with the deposited current, main
+// loop steps 6, 11, 12), and zeroing of the other current buffer.
+template <typename R>
+__global__ void k_e_advance(Geom g, FieldPtrs<R> f, const R *J0, const R *J1, const R *J2, R *Z0, R *Z1, R *Z2,
+                            R dt) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+        int pi, pj, pk;
+        padded_coords(g, p, pi, pj, pk);
+        const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
+        const long long c = g.pidx(i, j, k);
+        const R bx = ld(f.b[0], c), by = ld(f.b[1], c), bz = ld(f.b[2], c);
+        const R curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
+        const R curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
+        const R curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
+        R ex = f.e[0][p] + dt * curl_x + folded_current(g, J0, i, j, k);
+        R ey = f.e[1][p] + dt * curl_y + folded_current(g, J1, i, j, k);
+        R ez = f.e[2][p] + dt * curl_z + folded_current(g, J2, i, j, k);
+        if (g.bcx == 1 && i == 0) { ey = R(0); ez = R(0); }   // tangential e vanishes on the wall
+        f.e[0][p] = ex;
+        f.e[1][p] = ey;
+        f.e[2][p] = ez;
+        Z0[p] = R(0);
+        Z1[p] = R(0);
+        Z2[p] = R(0);
+    }
+}
+
+// Staggered value read by the gather; with conductor walls a value located
+// inside the conductor, or a tangential e / normal b on the wall, reads zero.
+__device__ inline float sval(const Geom &g, const float *a, bool xstag, int i, int j, int k) {
+    if (g.bcx == 1) {
+        if (xstag) { if (i < 0 || i > g.nx - 1) return 0.f; }
+        else { if (i <= 0 || i >= g.nx) return 0.f; }
+    }
+    return __ldg(a + g.widx(i, j, k));
+}
+
+// Node-averaged fields (App. A.3.3) at every padded node: e over its two edge
+// neighbours, b over its four face neighbours.  Stored as two float4 per node.
+__global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nf) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+        int pi, pj, pk;
+        padded_coords(g, p, pi, pj, pk);
+        // node coordinate (not wrapped: the conductor masking needs the true x)
+        int i = pi - g.G;
+        const int j = pj - g.G, k = pk - g.Gz;
+        if (g.bcx == 0) i = g.wx(i);
+        float E[3], B[3];
+        E[0] = 0.5f * (sval(g, f.e[0], true, i - 1, j, k) + sval(g, f.e[0], true, i, j, k));
+        E[1] = 0.5f * (sval(g, f.e[1], false, i, j - 1, k) + sval(g, f.e[1], false, i, j, k));
+        E[2] = 0.5f * (sval(g, f.e[2], false, i, j, k - 1) + sval(g, f.e[2], false, i, j, k));
+        B[0] = 0.25f * (sval(g, f.b[0], false, i, j, k) + sval(g, f.b[0], false, i, j - 1, k) +
+                        sval(g, f.b[0], false, i, j, k - 1) + sval(g, f.b[0], false, i, j - 1, k - 1));
+        B[1] = 0.25f * (sval(g, f.b[1], true, i, j, k) + sval(g, f.b[1], true, i - 1, j, k) +
+                        sval(g, f.b[1], true, i, j, k - 1) + sval(g, f.b[1], true, i - 1, j, k - 1));
+        B[2] = 0.25f * (sval(g, f.b[2], true, i, j, k) + sval(g, f.b[2], true, i - 1, j, k) +
+                        sval(g, f.b[2], true, i - 1, j - 1, k) + sval(g, f.b[2], true, i, j - 1, k));
+        nf[2 * p] = make_float4(E[0], E[1], E[2], B[0]);
+        nf[2 * p + 1] = make_float4(B[1], B[2], 0.f, 0.f);
+    }
+}
+
+template <typename R>
+__global__ void k_add_uniform(Geom g, FieldPtrs<R> f, R e0, R e1, R e2, R b0, R b1, R b2) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+        int pi, pj, pk;
+        padded_coords(g, p, pi, pj, pk);
+        const int i = g.wx(pi - g.G);
+        R v[6] = {e0, e1, e2, b0, b1, b2};
+        if (g.bcx == 1 && i == 0) { v[1] = R(0); v[2] = R(0); v[3] = R(0); }
+        f.e[0][p] += v[0]; f.e[1][p] += v[1]; f.e[2][p] += v[2];
+        f.b[0][p] += v[3]; f.b[1][p] += v[4]; f.b[2][p] += v[5];
+    }
+}
+
+inline int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    const long long cap = 152LL * 16;   // 16 resident 256-thread blocks per SM on 152 SMs
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+template <typename R>
+void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, double *energy_acc, cudaStream_t s) {
+    k_b_advance<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, h, energy_acc);
+}
+
+template <typename R>
+void launch_e_advance(const Geom &g, FieldPtrs<R> f, const R *const J[3], R *const Jzero[3], R dt,
+                      cudaStream_t s) {
+    k_e_advance<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, J[0], J[1], J[2], Jzero[0], Jzero[1], Jzero[2],
+                                                           dt);
+}
+
+void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nf, cudaStream_t s) {
+    k_node_fields<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, nf);
+}
+
+template <typename R>
+void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s) {
+    k_add_uniform<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, (R)e0[0], (R)e0[1], (R)e0[2], (R)b0[0],
+                                                             (R)b0[1], (R)b0[2]);
+}
+
+template void launch_b_advance<float>(const Geom &, FieldPtrs<float>, float, double *, cudaStream_t);
+template void launch_b_advance<double>(const Geom &, FieldPtrs<double>, double, double *, cudaStream_t);
+template void launch_e_advance<float>(const Geom &, FieldPtrs<float>, const float *const[3], float *const[3], float,
+                                      cudaStream_t);
+template void launch_e_advance<double>(const Geom &, FieldPtrs<double>, const double *const[3], double *const[3],
+                                       double, cudaStream_t);
+template void launch_add_uniform<float>(const Geom &, FieldPtrs<float>, const double[3], const double[3],
+                                        cudaStream_t);
+template void launch_add_uniform<double>(const Geom &, FieldPtrs<double>, const double[3], const double[3],
+                                         cudaStream_t);
+
+}  // namespace pic

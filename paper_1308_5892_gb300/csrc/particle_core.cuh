@@ -1,0 +1,149 @@
+// particle_core.cuh -- per-particle arithmetic shared by the FP64 and the
+// mixed-precision push kernels: the relativistic Boris step (App. A.3.3) and
+// the charge-conserving current of one straight segment inside one cell
+// (App. A.1, A.3.4, Eq. current_dep).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pic {
+
+template <typename R> __device__ inline R rsqrt_(R x);
+template <> __device__ inline float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+
+// Boris step with h = (q/e)(m_e/m), fields E, B at the particle:
+//   u- = u + h E dt/2;  gamma = sqrt(1 + u-^2);  t = h B dt/(2 gamma);
+//   s = 2t/(1+t^2);  u' = u- + u- x t;  u+ = u- + u' x s;  u <- u+ + h E dt/2.
+// This is the exact solution of the implicit rotation (u+ - u-)/dt =
+// h/(2 gamma) (u+ + u-) x B of Eq. mover1.
+template <typename R>
+__device__ inline void boris(R u[3], const R E[3], const R B[3], R h, R dt) {
+    const R qe = h * dt * R(0.5);
+    R um[3] = {u[0] + qe * E[0], u[1] + qe * E[1], u[2] + qe * E[2]};
+    const R inv_gam = rsqrt_<R>(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const R qb = qe * inv_gam;
+    const R t[3] = {qb * B[0], qb * B[1], qb * B[2]};
+    const R f = R(2) / (R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const R s[3] = {f * t[0], f * t[1], f * t[2]};
+    const R up[3] = {um[0] + (um[1] * t[2] - um[2] * t[1]), um[1] + (um[2] * t[0] - um[0] * t[2]),
+                     um[2] + (um[0] * t[1] - um[1] * t[0])};
+    u[0] = um[0] + (up[1] * s[2] - up[2] * s[1]) + qe * E[0];
+    u[1] = um[1] + (up[2] * s[0] - up[0] * s[2]) + qe * E[1];
+    u[2] = um[2] + (up[0] * s[1] - up[1] * s[0]) + qe * E[2];
+}
+
+// Current of one straight segment inside cell (ci, cj, ck): the particle (a
+// cube of volume 1) starts at offset d within the cell and moves by D.  With
+// mid-point weights W^0 = 1 - (d + D/2), W^1 = d + D/2, the flux through the x
+// face at (i+1/2, j+eta, k+xi) is D_x [W_y^eta W_z^xi + (-1)^(eta+xi) D_y D_z/12]
+// (the exact time integral of the overlap area), and enters Ampere's law as
+// -alpha times that flux; y and z by cyclic permutation.  In 2D3V the cube is
+// uniform along z: in-plane fluxes D_x W_y^eta and D_y W_x^eps, and the
+// out-of-plane flux D_z [W_x^eps W_y^eta + (-1)^(eps+eta) D_x D_y / 12] goes to
+// e_z at node (i+eps, j+eta).  sink(comp, di, dj, dk, value) receives -alpha F
+// for the current component comp at cell offset (di,dj,dk) from (ci,cj,ck).
+template <int NDIM, typename R, class Sink>
+__device__ inline void deposit_segment(const R d[3], const R D[3], R alpha, Sink &sink) {
+    R w1[3], w0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w1[a] = d[a] + R(0.5) * D[a];
+        w0[a] = R(1) - w1[a];
+    }
+    if (NDIM == 3) {
+        const R cyz = D[1] * D[2] * R(1.0 / 12.0), czx = D[2] * D[0] * R(1.0 / 12.0),
+                cxy = D[0] * D[1] * R(1.0 / 12.0);
+        const R ax = -alpha * D[0], ay = -alpha * D[1], az = -alpha * D[2];
+        // x faces (i+1/2, j+p, k+q)
+        sink(0, 0, 0, 0, ax * (w0[1] * w0[2] + cyz));
+        sink(0, 0, 1, 0, ax * (w1[1] * w0[2] - cyz));
+        sink(0, 0, 0, 1, ax * (w0[1] * w1[2] - cyz));
+        sink(0, 0, 1, 1, ax * (w1[1] * w1[2] + cyz));
+        // y faces (i+q, j+1/2, k+p)
+        sink(1, 0, 0, 0, ay * (w0[2] * w0[0] + czx));
+        sink(1, 1, 0, 0, ay * (w0[2] * w1[0] - czx));
+        sink(1, 0, 0, 1, ay * (w1[2] * w0[0] - czx));
+        sink(1, 1, 0, 1, ay * (w1[2] * w1[0] + czx));
+        // z faces (i+p, j+q, k+1/2)
+        sink(2, 0, 0, 0, az * (w0[0] * w0[1] + cxy));
+        sink(2, 1, 0, 0, az * (w1[0] * w0[1] - cxy));
+        sink(2, 0, 1, 0, az * (w0[0] * w1[1] - cxy));
+        sink(2, 1, 1, 0, az * (w1[0] * w1[1] + cxy));
+    } else {
+        const R ax = -alpha * D[0], ay = -alpha * D[1], az = -alpha * D[2];
+        const R cxy = D[0] * D[1] * R(1.0 / 12.0);
+        sink(0, 0, 0, 0, ax * w0[1]);
+        sink(0, 0, 1, 0, ax * w1[1]);
+        sink(1, 0, 0, 0, ay * w0[0]);
+        sink(1, 1, 0, 0, ay * w1[0]);
+        sink(2, 0, 0, 0, az * (w0[0] * w0[1] + cxy));
+        sink(2, 1, 0, 0, az * (w1[0] * w0[1] - cxy));
+        sink(2, 0, 1, 0, az * (w0[0] * w1[1] - cxy));
+        sink(2, 1, 1, 0, az * (w1[0] * w1[1] + cxy));
+    }
+}
+
+// Straight path from offset d0 in the start cell to the stored end: per axis a,
+// shift s[a] in {-1,0,1} cells and end offset d1[a] in the end cell.  The path
+// is split at the node planes it crosses (at most one per axis), segments in
+// increasing crossing parameter, ties in axis order; each piece is deposited
+// in its own cell by deposit_segment.  Positions at the breakpoints are taken
+// from the stored values (plane, stored end) so the segment displacements
+// telescope to the stored total and charge is conserved to rounding of the
+// fluxes.  dz2d is the out-of-plane displacement in 2D3V, shared between the
+// segments in proportion to their parameter length.  cell_sink(di,dj,dk)
+// re-targets the sink to the segment's cell (offset from the start cell).
+template <int NDIM, typename R, class Sink>
+__device__ inline void deposit_path(const R d0[3], const int s[3], const R d1[3], R dz2d, R alpha, Sink &sink) {
+    R tc[3], dv[3], plo[3], pnew[3];
+    bool crossed[3] = {false, false, false};
+    int ncross = 0;
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        plo[a] = s[a] > 0 ? R(1) : R(0);   // crossing plane in start-cell coordinates
+        pnew[a] = s[a] > 0 ? R(0) : R(1);  // the same plane in end-cell coordinates
+        if (s[a] != 0) {
+            const R first = plo[a] - d0[a];
+            const R second = d1[a] - pnew[a];
+            dv[a] = first + second;
+            tc[a] = dv[a] != R(0) ? first / dv[a] : R(0);
+            ++ncross;
+        } else {
+            dv[a] = d1[a] - d0[a];
+            tc[a] = R(2);
+        }
+    }
+    R cur[3] = {d0[0], d0[1], NDIM == 3 ? d0[2] : R(0)};
+    int cs[3] = {0, 0, 0};
+    R tprev = R(0);
+    for (int seg = 0; seg <= ncross; ++seg) {
+        // next crossing: smallest tc among axes not yet crossed (ties: lowest axis)
+        int ax = -1;
+        R tn = R(1);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a)
+            if (s[a] != 0 && !crossed[a] && (ax < 0 || tc[a] < tn)) { ax = a; tn = tc[a]; }
+        if (ax < 0) tn = R(1);
+        R D[3], endp[3];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            if (a == ax) endp[a] = plo[a];
+            else if (ax < 0) endp[a] = d1[a];
+            else if (crossed[a]) endp[a] = pnew[a] + dv[a] * (tn - tc[a]);
+            else endp[a] = d0[a] + dv[a] * tn;
+            D[a] = endp[a] - cur[a];
+        }
+        if (NDIM == 2) { D[2] = dz2d * (tn - tprev); cur[2] = R(0); }
+        sink.set_cell(cs[0], cs[1], cs[2]);
+        deposit_segment<NDIM, R>(cur, D, alpha, sink);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) cur[a] = endp[a];
+        if (ax < 0) break;
+        cur[ax] = pnew[ax];
+        cs[ax] = s[ax];
+        crossed[ax] = true;
+        tprev = tn;
+    }
+}
+
+}  // namespace pic

@@ -1,0 +1,148 @@
+// pic_internal.cuh -- shared declarations of the GB300 PIC library (not part of the ABI).
+//
+// Units and staggering follow the paper (App. A.2, A.3.2): cells of size 1,
+// time in X0/c, fields e and b = cB in m_e c^2/(e X0).  Field component c at
+// interior index (i,j,k): e_x (i+1/2,j,k), e_y (i,j+1/2,k), e_z (i,j,k+1/2),
+// b_x (i,j+1/2,k+1/2), b_y (i+1/2,j,k+1/2), b_z (i+1/2,j+1/2,k).
+//
+// Device layout (HBM):
+//  - every grid array is padded by G ghost cells on both sides of each
+//    simulated axis (z is not padded in 2D); padded index of interior (i,j,k)
+//    is ((k+Gz)*py + (j+G))*px + (i+G), px = nx+2G, ...  Ghost cells hold the
+//    periodic images of the interior, so a tile plus halo is one contiguous box.
+//  - fields: 6 planes e_x..b_z of Real; currents: 2 buffers x 3 planes (one is
+//    accumulated while the other is zeroed); node fields (mixed path): one
+//    float4 pair per padded cell, {E_x,E_y,E_z,B_x} {B_y,B_z,0,0}, the node
+//    averages of App. A.3.3 at time t.
+//  - particles, FP64 path: SoA planes x,y,z,u_x,u_y,u_z of double (absolute
+//    positions); mixed path: packed cell coordinates (uint32), FP32 offsets
+//    (SoA), FP32 momenta (SoA) and an int32 id, kept sorted by tile.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+// Device-side error bits (written with atomicOr into ctx error word).
+enum : int {
+    ERR_FAST_MOVE = 1,   // a particle moved more than one cell in a step
+    ERR_TIMEOUT = 2,     // a bounded spin gave up
+    ERR_NONFINITE = 4,   // non-finite value met
+    ERR_SORT = 8,        // sort bookkeeping overflow
+};
+
+struct Geom {
+    int ndim, nx, ny, nz;
+    int G, Gz;            // ghost width in x,y and in z (0 in 2D)
+    int px, py, pz;       // padded extents
+    long long pcells;     // px*py*pz
+    int bcx;              // 0 periodic, 1 conductor walls at x = 0, nx
+    __host__ __device__ inline long long pidx(int i, int j, int k) const {
+        return ((long long)(k + Gz) * py + (j + G)) * px + (i + G);
+    }
+    __host__ __device__ inline int wx(int i) const { int r = i % nx; return r < 0 ? r + nx : r; }
+    __host__ __device__ inline int wy(int j) const { int r = j % ny; return r < 0 ? r + ny : r; }
+    __host__ __device__ inline int wz(int k) const { int r = k % nz; return r < 0 ? r + nz : r; }
+    // padded index of the interior image of any integer coordinate
+    __host__ __device__ inline long long widx(int i, int j, int k) const { return pidx(wx(i), wy(j), wz(k)); }
+};
+
+// Packed cell coordinates of the mixed path: 2D i | j<<16; 3D i | j<<11 | k<<22.
+__host__ __device__ inline uint32_t pack_cell(int ndim, int i, int j, int k) {
+    return ndim == 2 ? (uint32_t)i | ((uint32_t)j << 16) : (uint32_t)i | ((uint32_t)j << 11) | ((uint32_t)k << 22);
+}
+__host__ __device__ inline void unpack_cell(int ndim, uint32_t c, int &i, int &j, int &k) {
+    if (ndim == 2) { i = c & 0xffff; j = c >> 16; k = 0; }
+    else { i = c & 0x7ff; j = (c >> 11) & 0x7ff; k = c >> 22; }
+}
+
+template <typename R>
+struct FieldPtrs {
+    R *e[3];
+    R *b[3];
+};
+
+struct Species64 {
+    double *x[3];
+    double *u[3];
+};
+
+struct SpeciesMixed {
+    uint32_t *cell;
+    float *off[3];
+    float *u[3];
+    int32_t *id;
+};
+
+struct TileGeom {
+    int T[3];        // tile extent in cells (T[2] = 1 in 2D)
+    int H;           // halo (cells) on each side, equal to the ghost width G
+    int R[3];        // T + 2H (R[2] = 1 in 2D)
+    int ntile[3];    // tiles per axis
+    int ntiles;
+    int cells_per_tile;
+};
+
+// ---- kernel launchers (implemented in the .cu files) ----
+
+// fields.cu
+template <typename R>
+void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, double *energy_acc, cudaStream_t s);
+template <typename R>
+void launch_e_advance(const Geom &g, FieldPtrs<R> f, const R *const J[3], R *const Jzero[3], R dt,
+                      cudaStream_t s);
+void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nf, cudaStream_t s);
+template <typename R>
+void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s);
+
+// push_fp64.cu
+void launch_push_fp64(const Geom &g, FieldPtrs<double> f, double *const J[3], Species64 sp, long long n,
+                      double h, double alpha, double dt, int mode, double m_over_me, double *kin_acc, int *err,
+                      cudaStream_t s);
+
+// push_mixed.cu
+struct MixedStepArgs {
+    Geom g;
+    TileGeom t;
+    const float4 *nf;          // node fields (padded, 2 float4 per cell)
+    float *J[3];               // padded current planes being accumulated
+    SpeciesMixed sp;
+    const int *tile_start;     // ntiles+1 offsets into the particle arrays
+    float h, alpha, dt;
+    int mode;                  // 0 step, 1 half step back (momenta only)
+    double *kin_acc;           // 2 doubles: kinetic energy of u^{t-1/2} and u^{t+1/2} (times m/m_e)
+    double m_over_me;
+    int *err;
+};
+void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
+size_t mixed_smem_bytes(const TileGeom &t, int ndim);
+
+// sort.cu
+struct SortArgs {
+    Geom g;
+    TileGeom t;
+    long long n;
+    SpeciesMixed src, dst;
+    int *counts;     // ntiles*cells_per_tile + 1 scratch
+    int *offsets;    // same size: exclusive scan; offsets[key] start of key
+    int *block_sums; // scratch for the scan
+    int *tile_start; // ntiles+1 output
+    int *err;
+};
+void launch_sort(const SortArgs &a, cudaStream_t s);
+size_t sort_scan_scratch(long long nkeys);
+
+// diag.cu
+template <typename R>
+void launch_field_diag(const Geom &g, FieldPtrs<R> f, double *acc /*6*/, long long *nonfinite, cudaStream_t s);
+void launch_particle_diag64(const Geom &g, Species64 sp, long long n, double m_over_me, double *acc /*8*/,
+                            long long *nonfinite, cudaStream_t s);
+void launch_particle_diag_mixed(const Geom &g, SpeciesMixed sp, long long n, double m_over_me, double *acc,
+                                long long *nonfinite, cudaStream_t s);
+template <typename R>
+void launch_div_e(const Geom &g, FieldPtrs<R> f, double *out /*ncell interior*/, cudaStream_t s);
+void launch_rho64(const Geom &g, Species64 sp, long long n, double alpha, double *rho, cudaStream_t s);
+void launch_rho_mixed(const Geom &g, SpeciesMixed sp, long long n, double alpha, double *rho, cudaStream_t s);
+void launch_max_abs_diff(const double *a, const double *b, long long n, double *out_max, cudaStream_t s);
+
+}  // namespace pic

@@ -1,0 +1,178 @@
+// sort.cu -- counting sort of the mixed-path particles by tile-major cell key.
+//
+// key(cell) = tile_index * cells_per_tile + index of the cell inside its tile,
+// so particles end up grouped by tile and, inside a tile, by cell.  The sort
+// is out of place (src -> dst, the caller swaps the buffers): histogram of the
+// keys, exclusive scan, and a scatter whose per-key cursors are advanced with
+// warp-aggregated atomics (lanes of a warp that share a key take consecutive
+// slots with one atomic).  The tile offsets are read from the scanned counts.
+//
+// Roofline: HBM bound; per particle 4 B (histogram) + 2 x (24..28 + 4) B
+// (scatter) plus per key 3 x 4 B.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <int NDIM>
+__device__ inline int cell_key(const TileGeom &t, uint32_t c) {
+    int i, j, k;
+    unpack_cell(NDIM, c, i, j, k);
+    const int ti = i / t.T[0], tj = j / t.T[1], tk = NDIM == 3 ? k / t.T[2] : 0;
+    const int li = i - ti * t.T[0], lj = j - tj * t.T[1], lk = NDIM == 3 ? k - tk * t.T[2] : 0;
+    const int tile = (tk * t.ntile[1] + tj) * t.ntile[0] + ti;
+    return tile * t.cells_per_tile + (lk * t.T[1] + lj) * t.T[0] + li;
+}
+
+__global__ void k_zero(int *a, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = 0;
+}
+
+template <int NDIM>
+__global__ void k_histogram(TileGeom t, const uint32_t *cell, long long n, int *counts, long long nkeys, int *err) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int key = cell_key<NDIM>(t, cell[p]);
+        if (key < 0 || key >= nkeys) { atomicOr(err, ERR_SORT); continue; }
+        // warp aggregation: lanes with the same key add once
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, key);
+        const int leader = __ffs(peers) - 1;
+        if ((int)(threadIdx.x & 31) == leader) atomicAdd(counts + key, __popc(peers));
+    }
+}
+
+// Block-level exclusive scan of kScanTile ints; returns the block total.
+__device__ inline int block_scan(int (&v)[kScanItems], int *sh) {
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) { const int x = v[q]; v[q] = local; local += x; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (kScanThreads / 32) ? sh[lane] : 0;
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        sh[lane] = wi - w;       // exclusive warp offsets
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    const int off = sh[warp] + incl - local;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] += off;
+    const int total = sh[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const int *in, int *out, int *block_sums, long long n) {
+    __shared__ int sh[33];
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] = base + q < n ? in[base + q] : 0;
+    const int total = block_scan(v, sh);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (base + q < n) out[base + q] = v[q];
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of the block sums in one block (any count, in chunks).
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *block_sums, int nb) {
+    __shared__ int sh[33];
+    int carry = 0;
+    for (int base = 0; base < nb; base += kScanTile) {
+        int v[kScanItems];
+        const int b0 = base + threadIdx.x * kScanItems;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) v[q] = b0 + q < nb ? block_sums[b0 + q] : 0;
+        const int total = block_scan(v, sh);
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q)
+            if (b0 + q < nb) block_sums[b0 + q] = v[q] + carry;
+        carry += total;
+    }
+}
+
+// Add block offsets; copy to cursors; extract tile offsets.
+__global__ void k_scan_finish(int *offsets, int *cursors, const int *block_sums, long long nkeys, int cells_per_tile,
+                              int ntiles, int *tile_start, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nkeys;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = offsets[i] + block_sums[i / kScanTile];
+        offsets[i] = v;
+        cursors[i] = v;
+        if (i % cells_per_tile == 0) tile_start[i / cells_per_tile] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tile_start[ntiles] = (int)n;
+}
+
+template <int NDIM>
+__global__ void k_scatter(TileGeom t, SpeciesMixed src, SpeciesMixed dst, long long n, int *cursors, long long nkeys) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = src.cell[p];
+        const int key = cell_key<NDIM>(t, c);
+        if (key < 0 || key >= nkeys) continue;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, key);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(cursors + key, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const int q = base + __popc(peers & ((1u << lane) - 1u));
+        dst.cell[q] = c;
+        dst.off[0][q] = src.off[0][p];
+        dst.off[1][q] = src.off[1][p];
+        if (NDIM == 3) dst.off[2][q] = src.off[2][p];
+        dst.u[0][q] = src.u[0][p];
+        dst.u[1][q] = src.u[1][p];
+        dst.u[2][q] = src.u[2][p];
+        dst.id[q] = src.id[p];
+    }
+}
+
+inline int blocks_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    const long long cap = 152LL * 32;
+    return (int)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+}  // namespace
+
+size_t sort_scan_scratch(long long nkeys) { return (size_t)((nkeys + kScanTile - 1) / kScanTile + 1); }
+
+void launch_sort(const SortArgs &a, cudaStream_t s) {
+    const long long nkeys = (long long)a.t.ntiles * a.t.cells_per_tile;
+    k_zero<<<blocks_for(nkeys, 256), 256, 0, s>>>(a.counts, nkeys);
+    if (a.n > 0) {
+        if (a.g.ndim == 3) k_histogram<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.err);
+        else k_histogram<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.err);
+    }
+    const int nb = (int)((nkeys + kScanTile - 1) / kScanTile);
+    k_scan_blocks<<<nb, kScanThreads, 0, s>>>(a.counts, a.offsets, a.block_sums, nkeys);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
+    k_scan_finish<<<blocks_for(nkeys, 256), 256, 0, s>>>(a.offsets, a.counts, a.block_sums, nkeys,
+                                                         a.t.cells_per_tile, a.t.ntiles, a.tile_start, a.n);
+    if (a.n > 0) {
+        if (a.g.ndim == 3) k_scatter<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src, a.dst, a.n, a.counts, nkeys);
+        else k_scatter<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src, a.dst, a.n, a.counts, nkeys);
+    }
+}
+
+}  // namespace pic

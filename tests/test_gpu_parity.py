@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+FP64 path: one step (and several) from an identical state, norm-wise relative
+difference <= 1e-12 per field component and per particle array.
+Mixed path: one step from the same FP32-rounded state, fields <= 1e-5
+relative (norm-wise), positions <= 2e-6 cells, momenta <= 1e-5 relative, and
+the Gauss residual of a neutral start <= 1e-6 of max |rho~_s|.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1308_5892_gb300 as pic
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _make(ndim, shape, ppc, seed, spread, amp, colocate, n_x=2.0, rho_sp0=8.0, dt=0.5, species=synth.PAIR):
+    nx, ny, nz = shape
+    arr = synth.random_state_arrays(seed, ndim, nx, ny, nz, ppc=ppc, spread=spread, amp_e=amp, amp_b=amp,
+                                    colocate=colocate, species=species)
+    n = arr["species"][0]["pos"].shape[1]
+    desc = pic.run_desc(ndim, nx, ny, nz if ndim == 3 else 1, n_x, rho_sp0, dt,
+                        [(s["q_over_e"], s["m_over_me"], n) for s in arr["species"]])
+    fields = np.concatenate([arr["e"], arr["b"]])
+    parts = [np.concatenate([s["pos"], s["u"]]) for s in arr["species"]]
+    return desc, fields, parts, arr
+
+
+def _oracle_state(desc, fields, parts, arr):
+    st = oracle.State.empty(desc.ndim, desc.nx, desc.ny, desc.nz, desc.dt, desc.n_x, desc.rho_sp0)
+    st.e[:] = fields[:3]
+    st.b[:] = fields[3:]
+    for s, p in zip(arr["species"], parts):
+        st.species.append(oracle.Species(np.ascontiguousarray(p[:3]), np.ascontiguousarray(p[3:]),
+                                         s["q_over_e"], s["m_over_me"]))
+    return st
+
+
+def _rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / den if den > 0 else np.abs(a - b).max()
+
+
+def _pos_diff(a, b, L):
+    d = a - b
+    return np.abs(d - L * np.round(d / L)).max()
+
+
+def _compare(desc, f_gpu, p_gpu, st, tol_field, tol_pos, tol_u):
+    ref_f = np.concatenate([st.e, st.b])
+    for c in range(6):
+        r = _rel(f_gpu[c], ref_f[c])
+        assert r <= tol_field, ("field component", c, r)
+    L = [desc.nx, desc.ny, desc.nz]
+    for s, sp in enumerate(st.species):
+        for a in range(desc.ndim):
+            d = _pos_diff(p_gpu[s][a], sp.pos[a], L[a])
+            assert d <= tol_pos, ("position", s, a, d)
+        for a in range(3):
+            r = _rel(p_gpu[s][3 + a], sp.u[a])
+            assert r <= tol_u, ("momentum", s, a, r)
+
+
+# ----------------------------------------------------------------- FP64 path
+
+@pytest.mark.parametrize("ndim,shape,ppc", [(2, (33, 20, 1), 4), (3, (12, 10, 9), 3)])
+def test_fp64_steps_match_oracle_to_1e12(ndim, shape, ppc):
+    desc, fields, parts, arr = _make(ndim, shape, ppc, seed=100 + ndim, spread=2.0, amp=0.05, colocate=False)
+    with pic.Context([desc], precision=pic.PIC_FP64) as ctx:
+        ctx.set_state(0, fields, parts)
+        st = _oracle_state(desc, fields, parts, arr)
+        for nsteps in (1, 4):
+            ctx.step(nsteps)
+            oracle.step(st, nsteps)
+            f, p, step = ctx.get_state(0)
+            _compare(desc, f, p, st, 1e-12, 1e-12 * max(shape), 1e-12)
+
+
+def test_fp64_diagnostics_match_oracle():
+    desc, fields, parts, arr = _make(2, (24, 16, 1), 6, seed=7, spread=1.0, amp=0.05, colocate=False)
+    with pic.Context([desc], precision=pic.PIC_FP64) as ctx:
+        ctx.set_state(0, fields, parts)
+        ctx.step(3)
+        d = ctx.diagnostics(0)
+        f, p, _ = ctx.get_state(0)
+    st = _oracle_state(desc, f, p, arr)
+    en = oracle.energies(st)
+    assert np.allclose(d["kinetic"], en["kinetic"], rtol=1e-12)
+    assert np.allclose(d["field_e"], en["field_e"], rtol=1e-12)
+    assert np.allclose(d["field_b"], en["field_b"], rtol=1e-12)
+    g, rmax = oracle.gauss_residual(st)
+    assert abs(d["gauss_max"] - g) <= 1e-12 * rmax
+    assert np.isclose(d["rho_max"], rmax, rtol=1e-12)
+    for s in range(2):
+        assert np.allclose(d["sum_u"][s], st.species[s].u.sum(1), rtol=1e-12, atol=1e-9)
+
+
+def test_fp64_neutral_start_keeps_gauss_to_roundoff():
+    desc, fields, parts, arr = _make(3, (10, 12, 8), 4, seed=9, spread=1.5, amp=0.0, colocate=True)
+    fields[3:] = np.random.default_rng(1).normal(0, 0.05, fields[3:].shape)
+    with pic.Context([desc], precision=pic.PIC_FP64) as ctx:
+        ctx.set_state(0, fields, parts)
+        ctx.step(20)
+        d = ctx.diagnostics(0)
+    assert d["gauss_max"] <= 1e-12 * d["rho_max"]
+
+
+# ----------------------------------------------------------------- mixed path
+
+def _mixed_roundtrip(desc, fields, parts, arr, **kw):
+    ctx = pic.Context([desc], precision=pic.PIC_MIXED, **kw)
+    ctx.set_state(0, fields, parts)
+    f0, p0, _ = ctx.get_state(0)
+    return ctx, _oracle_state(desc, f0, p0, arr)
+
+
+@pytest.mark.parametrize("ndim,shape,ppc", [(2, (64, 40, 1), 8), (3, (20, 16, 12), 4), (2, (7, 5, 1), 5)])
+def test_mixed_one_step_matches_oracle(ndim, shape, ppc):
+    desc, fields, parts, arr = _make(ndim, shape, ppc, seed=200 + ndim, spread=1.0, amp=0.05, colocate=False)
+    ctx, st = _mixed_roundtrip(desc, fields, parts, arr)
+    with ctx:
+        ctx.step(1)
+        f, p, _ = ctx.get_state(0)
+    oracle.step(st)
+    _compare(desc, f, p, st, 1e-5, 2e-6, 1e-5)
+
+
+@pytest.mark.parametrize("ndim,shape", [(2, (48, 32, 1)), (3, (16, 16, 16))])
+def test_mixed_neutral_start_gauss_residual(ndim, shape):
+    desc, fields, parts, arr = _make(ndim, shape, 8, seed=300 + ndim, spread=1.0, amp=0.0, colocate=True)
+    fields[3:] = np.random.default_rng(2).normal(0, 0.05, fields[3:].shape)
+    with pic.Context([desc], precision=pic.PIC_MIXED) as ctx:
+        ctx.set_state(0, fields, parts)
+        ctx.step(1)
+        d1 = ctx.diagnostics(0)
+        ctx.step(19)
+        d20 = ctx.diagnostics(0)
+    assert d1["gauss_max"] <= 1e-6 * d1["rho_max"], d1
+    # 20 steps, with re-sorts: still within the same bound
+    assert d20["gauss_max"] <= 1e-6 * d20["rho_max"], d20
+
+
+@pytest.mark.parametrize("sort_interval", [1, 4, 1000])
+def test_mixed_multistep_with_sorting_and_halo_escape(sort_interval):
+    """12 steps; with sort_interval = 1000 particles drift out of the staged
+    halo of their tile and take the global slow path."""
+    desc, fields, parts, arr = _make(2, (48, 40, 1), 6, seed=400, spread=3.0, amp=0.02, colocate=False)
+    ctx, st = _mixed_roundtrip(desc, fields, parts, arr, sort_interval=sort_interval)
+    with ctx:
+        ctx.step(12)
+        f, p, _ = ctx.get_state(0)
+    oracle.step(st, 12)
+    # FP32 vs FP64 over 12 steps: differences grow from 1e-7 per step
+    _compare(desc, f, p, st, 2e-4, 1e-4, 2e-4)
+
+
+def test_mixed_empty_species_and_boundary_positions():
+    desc, fields, parts, arr = _make(2, (32, 32, 1), 2, seed=5, spread=0.7, amp=0.03, colocate=False)
+    n = parts[0].shape[1]
+    # positions on node planes, on the periodic seam and just below a cell edge
+    parts[0][0, :8] = [0.0, 1.0, 31.0, 31.999999999, 16.0, 0.5, 15.9999999999, 2.0]
+    parts[0][1, :8] = [0.0, 31.99999999999, 5.0, 7.0, 16.0, 0.0, 3.0, 31.0]
+    parts[1] = np.zeros((6, 0))
+    desc.species[1].capacity = 0
+    ctx, st = _mixed_roundtrip(desc, fields, parts, arr)
+    st.species[1] = oracle.Species(np.zeros((3, 0)), np.zeros((3, 0)), 1.0, 1.0)
+    with ctx:
+        ctx.step(1)
+        f, p, _ = ctx.get_state(0)
+    oracle.step(st)
+    assert p[1].shape == (6, 0)
+    _compare(desc, f, p[:1] + [np.zeros((6, 0))], st, 1e-5, 2e-6, 1e-5)
+
+
+def test_mixed_energy_history_tracks_oracle():
+    desc, fields, parts, arr = _make(2, (32, 32, 1), 8, seed=11, spread=0.5, amp=0.0, colocate=True)
+    ctx, st = _mixed_roundtrip(desc, fields, parts, arr)
+    with ctx:
+        ctx.step(10)
+        hist = ctx.energy_history(0)
+    assert hist.shape == (10, 4)
+    # step 0 kinetic at t_0 is the average of gamma-1 over u^{-1/2} and u^{1/2}
+    ek_minus = sum(sp.m_over_me * (np.sqrt(1 + (sp.u ** 2).sum(0)) - 1).sum() for sp in st.species)
+    oracle.step(st)
+    ek_plus = sum(sp.m_over_me * (np.sqrt(1 + (sp.u ** 2).sum(0)) - 1).sum() for sp in st.species)
+    assert np.isclose(hist[0, 0], 0.5 * (ek_minus + ek_plus), rtol=1e-5)
+    assert np.all(np.isfinite(hist))
