@@ -32,6 +32,10 @@ WORKLOADS = {
                           nz=128, ppc=32, theta=1.0, n_x=1.0, rho_sp0=64.0, dt=0.5),
     "thermal2d_1024": dict(name="2D3V thermal pair plasma 1024^2, 50 ppc/species, theta=0.01", ndim=2, nx=1024,
                            ny=1024, nz=1, ppc=50, theta=0.01, n_x=20.0, rho_sp0=100.0, dt=0.5),
+    "thermal3d_64": dict(name="3D3V thermal pair plasma 64^3, 32 ppc/species, theta=1", ndim=3, nx=64, ny=64,
+                         nz=64, ppc=32, theta=1.0, n_x=1.0, rho_sp0=64.0, dt=0.5),
+    "thermal2d_512": dict(name="2D3V thermal pair plasma 512^2, 50 ppc/species, theta=0.01", ndim=2, nx=512,
+                          ny=512, nz=1, ppc=50, theta=0.01, n_x=20.0, rho_sp0=100.0, dt=0.5),
     "thermal2d_64": dict(name="2D3V thermal pair plasma 64^2, 16 ppc/species, theta=0.1", ndim=2, nx=64, ny=64, nz=1,
                          ppc=16, theta=0.1, n_x=0.1 ** -0.5, rho_sp0=32.0, dt=0.5),
 }
@@ -190,9 +194,11 @@ def run_ours(args, w):
                         [(-1.0, 1.0, n), (1.0, 1.0, n)])
     npart = 2 * n
     results = {}
-    for prec, name in ((pic.PIC_MIXED, "mixed"), (pic.PIC_FP64, "fp64")):
+    legs = ((pic.PIC_MIXED, "mixed"),) if args.no_fp64 else ((pic.PIC_MIXED, "mixed"), (pic.PIC_FP64, "fp64"))
+    for prec, name in legs:
         steps = args.steps if prec == pic.PIC_MIXED else max(1, min(args.steps, args.fp64_steps))
-        ctx = pic.Context([desc], precision=prec, flags=pic.PIC_FLAG_TIMING)
+        ctx = pic.Context([desc], precision=prec, flags=pic.PIC_FLAG_TIMING, tile=tuple(args.tile),
+                          sort_interval=args.sort_interval)
         ctx.set_state(0, fields, parts)
         ctx.step(args.warmup)
         ctx.kernel_time(pic.PIC_KERNEL_PUSH, reset=True)
@@ -227,6 +233,17 @@ def run_ours(args, w):
 
     # end-to-end through the C ABI with host buffers: upload the state, run the
     # timed steps, read the state back; all copies inside the timed region
+    e2e_s = None
+    h2d = fields.nbytes + sum(p.nbytes for p in parts)
+    d2h = h2d
+    if not args.no_e2e:
+        e2e_s = _e2e(pic, torch, desc, fields, parts, args, barrier)
+    if args.no_fp64:
+        results["fp64"] = None
+    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist)
+
+
+def _e2e(pic, torch, desc, fields, parts, args, barrier):
     pin_f = torch.from_numpy(fields).pin_memory().numpy()
     pin_p = [torch.from_numpy(p).pin_memory().numpy() for p in parts]
     out_f = torch.empty(fields.shape, dtype=torch.float64).pin_memory().numpy()
@@ -242,9 +259,10 @@ def run_ours(args, w):
     barrier()
     e2e_s = time.perf_counter() - t0
     ctx.close()
-    h2d = fields.nbytes + sum(p.nbytes for p in parts)
-    d2h = h2d
+    return e2e_s
 
+
+def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist):
     m = results["mixed"]
     value_rank = npart * m["steps"] / (m["ms"] * 1e6)
     value = value_rank * world
@@ -262,16 +280,18 @@ def run_ours(args, w):
             "config": {"workload": w["name"], "particles_per_gpu": npart, "cells": w["nx"] * w["ny"] * (w["nz"] if w["ndim"] == 3 else 1),
                        "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 (%.1f GB particle state)" % (npart * 28 / 1e9),
                        "tuning": m["tuning"]},
-            "fp64": {"value": npart * f64["steps"] / (f64["ms"] * 1e6) * world, "unit": "particle-steps/ns",
-                     "ms_per_step": f64["ms"] / f64["steps"], "steps": f64["steps"]},
+            "fp64": None if f64 is None else {"value": npart * f64["steps"] / (f64["ms"] * 1e6) * world,
+                                              "unit": "particle-steps/ns", "ms_per_step": f64["ms"] / f64["steps"],
+                                              "steps": f64["steps"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "k_push_mixed (gather+push+deposit, both species)",
                          "peak_kind": peak_kind, "push_ms_per_step": push_launch_ms,
                          "field_ms_per_step": m["field_ms"] / m["steps"], "sort_ms_total": m["sort_ms"]},
             "cpu_baseline": None,
-            "e2e": {"value": npart * args.steps / (e2e_s * 1e9) * world, "unit": "particle-steps/ns",
-                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "note": "set_state from pinned host + steps + get_state to pinned host"},
+            "e2e": None if e2e_s is None else {
+                "value": npart * args.steps / (e2e_s * 1e9) * world, "unit": "particle-steps/ns",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "note": "set_state from pinned host + steps + get_state to pinned host"},
             "gpu_launches": int(m["counters"]["launches_per_step"] * m["steps"]),
             "clocks": m["clocks"],
             "diag": {"gauss_max": m["diag"]["gauss_max"], "rho_max": m["diag"]["rho_max"]},
@@ -296,6 +316,10 @@ def main():
     ap.add_argument("--workload", default="thermal3d_128", choices=sorted(WORKLOADS))
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--tile", type=int, nargs=3, default=(0, 0, 0))
+    ap.add_argument("--sort-interval", type=int, default=0)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

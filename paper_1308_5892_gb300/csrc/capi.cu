@@ -40,11 +40,13 @@ struct Run {
     int since_sort = 0;
     bool sorted = false;
     void *F = nullptr;          // 6 planes of Real (e_x..b_z), padded
-    void *J = nullptr;          // 2 buffers x 3 planes of Real, padded
+    void *J = nullptr;          // 2 buffers x 3 planes, padded: double (FP64) or int64 fixed point (mixed)
     int jcur = 0;
-    float4 *nf = nullptr;       // node fields (mixed)
+    float4 *nfA = nullptr;      // node fields {E_x,E_y,E_z,B_x} (mixed)
+    float2 *nfB = nullptr;      // node fields {B_y,B_z} (mixed)
     SpeciesState sp[PIC_MAX_SPECIES];
     int *counts = nullptr, *offsets = nullptr, *block_sums = nullptr;
+    int *perm = nullptr;        // sort scratch, max species capacity
     double *rho_s = nullptr, *rho_tot = nullptr, *divb = nullptr;
     double *acc = nullptr;      // diagnostics accumulators (64 doubles)
     double *hist = nullptr;     // energy history, 8 doubles per step
@@ -150,8 +152,10 @@ FieldPtrs<R> fields_of(Run &r) {
     return f;
 }
 
+// Both current types (double, int64) are 8 bytes wide.
 template <typename R>
 R *jplane(Run &r, int buf, int c) {
+    static_assert(sizeof(R) == 8, "current planes are 8-byte values");
     return (R *)r.J + ((size_t)buf * 3 + c) * r.g.pcells;
 }
 
@@ -312,17 +316,21 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     const size_t rs = real_size(ctx);
     const long long ncell = (long long)g.nx * g.ny * g.nz;
     r.F = dev_alloc(ctx, 6 * rs * g.pcells);
-    r.J = dev_alloc(ctx, 6 * rs * g.pcells);
+    r.J = dev_alloc(ctx, 6 * 8 * g.pcells);
     if (!r.F || !r.J) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the field arrays");
     CK(cudaMemsetAsync(r.F, 0, 6 * rs * g.pcells, ctx->stream));
-    CK(cudaMemsetAsync(r.J, 0, 6 * rs * g.pcells, ctx->stream));
+    CK(cudaMemsetAsync(r.J, 0, 6 * 8 * g.pcells, ctx->stream));
     if (mixed) {
-        r.nf = (float4 *)dev_alloc(ctx, 2 * sizeof(float4) * g.pcells);
+        r.nfA = (float4 *)dev_alloc(ctx, sizeof(float4) * g.pcells);
+        r.nfB = (float2 *)dev_alloc(ctx, sizeof(float2) * g.pcells);
         const long long nkeys = (long long)r.t.ntiles * r.t.cells_per_tile;
         r.counts = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.offsets = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.block_sums = (int *)dev_alloc(ctx, sizeof(int) * sort_scan_scratch(nkeys));
-        if (!r.nf || !r.counts || !r.offsets || !r.block_sums)
+        int64_t capmax = 1;
+        for (int s = 0; s < d.nspecies; ++s) capmax = std::max<int64_t>(capmax, d.species[s].capacity);
+        r.perm = (int *)dev_alloc(ctx, sizeof(int) * capmax);
+        if (!r.nfA || !r.nfB || !r.counts || !r.offsets || !r.block_sums || !r.perm)
             return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the tile buffers");
     }
     r.rho_s = (double *)dev_alloc(ctx, sizeof(double) * ncell);
@@ -402,6 +410,7 @@ void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
     a.offsets = r.offsets;
     a.block_sums = r.block_sums;
     a.tile_start = S.tile_start;
+    a.perm = r.perm;
     a.err = ctx->d_err;
     launch_sort(a, ctx->stream);
     S.cur = 1 - S.cur;
@@ -442,44 +451,48 @@ void step_run(pic_ctx *ctx, Run &r) {
             for (int q = 0; q < nsp; ++q) sort_species(ctx, r, r.sp[q]);
             r.sorted = true;
             r.since_sort = 0;
-            launches += 6 * nsp;
+            launches += 7 * nsp;
         }
         FieldPtrs<float> f = fields_of<float>(r);
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
             launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, hslot ? hslot + 2 : nullptr, s);
-            launch_node_fields(r.g, f, r.nf, s);
+            launch_node_fields(r.g, f, r.nfA, r.nfB, s);
         }
-        float *J[3] = {jplane<float>(r, r.jcur, 0), jplane<float>(r, r.jcur, 1), jplane<float>(r, r.jcur, 2)};
-        KTimer* tp = new KTimer(ctx, PIC_KERNEL_PUSH);
-        for (int q = 0; q < nsp; ++q) {
-            SpeciesState &S = r.sp[q];
+        typedef unsigned long long u64;
+        u64 *J[3] = {jplane<u64>(r, r.jcur, 0), jplane<u64>(r, r.jcur, 1), jplane<u64>(r, r.jcur, 2)};
+        {
+            KTimer t(ctx, PIC_KERNEL_PUSH);
             MixedStepArgs a;
             a.g = r.g;
             a.t = r.t;
-            a.nf = r.nf;
+            a.nfA = r.nfA;
+            a.nfB = r.nfB;
             for (int c = 0; c < 3; ++c) a.J[c] = J[c];
-            a.sp = S.mb[S.cur];
-            a.tile_start = S.tile_start;
-            a.h = (float)S.h;
-            a.alpha = (float)S.alpha;
+            a.nspecies = nsp;
+            for (int q = 0; q < nsp; ++q) {
+                SpeciesState &S = r.sp[q];
+                a.sp[q] = S.mb[S.cur];
+                a.tile_start[q] = S.tile_start;
+                a.h[q] = (float)S.h;
+                a.sgn[q] = S.q_over_e > 0 ? 1.f : -1.f;
+                a.m_over_me[q] = S.m_over_me;
+            }
             a.dt = (float)r.d.dt;
             a.mode = 0;
             a.kin_acc = hslot;
-            a.m_over_me = S.m_over_me;
             a.err = ctx->d_err;
             launch_push_mixed(a, s);
         }
-        delete tp;
-        float *Z[3] = {jplane<float>(r, 1 - r.jcur, 0), jplane<float>(r, 1 - r.jcur, 1), jplane<float>(r, 1 - r.jcur, 2)};
-        const float *Jc[3] = {J[0], J[1], J[2]};
+        u64 *Z[3] = {jplane<u64>(r, 1 - r.jcur, 0), jplane<u64>(r, 1 - r.jcur, 1), jplane<u64>(r, 1 - r.jcur, 2)};
+        const u64 *Jc[3] = {J[0], J[1], J[2]};
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
             launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, nullptr, s);
-            launch_e_advance<float>(r.g, f, Jc, Z, (float)r.d.dt, s);
+            launch_e_advance_fx(r.g, f, Jc, Z, (float)r.d.dt, 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0), s);
         }
         r.since_sort++;
-        launches += 4 + nsp;
+        launches += 5;
         ctx->launches_per_step = launches;
         ctx->bytes_per_ps = r.d.ndim == 2 ? 48.0 : 56.0;
     }
@@ -591,7 +604,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
             k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (float *)r.F + c * g.pcells);
         CK(cudaGetLastError());
     }
-    CK(cudaMemsetAsync(r.J, 0, 6 * rs * g.pcells, sm));
+    CK(cudaMemsetAsync(r.J, 0, 6 * 8 * g.pcells, sm));
     r.jcur = 0;
     for (int s = 0; s < r.d.nspecies; ++s) {
         SpeciesState &S = r.sp[s];

@@ -135,6 +135,37 @@ __global__ void k_e_advance(Geom g, FieldPtrs<R> f, const R *J0, const R *J1, co
     }
 }
 
+// Mixed path: the same update with the fixed-point current (int64, units of
+// 2^-36 of sgn(q) times the volume flux); scale = |alpha| 2^-36.
+__global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long long *J0,
+                               const unsigned long long *J1, const unsigned long long *J2, unsigned long long *Z0,
+                               unsigned long long *Z1, unsigned long long *Z2, float dt, double scale) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+        int pi, pj, pk;
+        padded_coords(g, p, pi, pj, pk);
+        const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
+        const long long c = g.pidx(i, j, k);
+        const float bx = ld(f.b[0], c), by = ld(f.b[1], c), bz = ld(f.b[2], c);
+        const float curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
+        const float curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
+        const float curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
+        const float jx = (float)(scale * (double)(long long)folded_current(g, J0, i, j, k));
+        const float jy = (float)(scale * (double)(long long)folded_current(g, J1, i, j, k));
+        const float jz = (float)(scale * (double)(long long)folded_current(g, J2, i, j, k));
+        float ex = f.e[0][p] + dt * curl_x + jx;
+        float ey = f.e[1][p] + dt * curl_y + jy;
+        float ez = f.e[2][p] + dt * curl_z + jz;
+        if (g.bcx == 1 && i == 0) { ey = 0.f; ez = 0.f; }
+        f.e[0][p] = ex;
+        f.e[1][p] = ey;
+        f.e[2][p] = ez;
+        Z0[p] = 0ull;
+        Z1[p] = 0ull;
+        Z2[p] = 0ull;
+    }
+}
+
 // Staggered value read by the gather; with conductor walls a value located
 // inside the conductor, or a tangential e / normal b on the wall, reads zero.
 __device__ inline float sval(const Geom &g, const float *a, bool xstag, int i, int j, int k) {
@@ -146,8 +177,8 @@ __device__ inline float sval(const Geom &g, const float *a, bool xstag, int i, i
 }
 
 // Node-averaged fields (App. A.3.3) at every padded node: e over its two edge
-// neighbours, b over its four face neighbours.  Stored as two float4 per node.
-__global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nf) {
+// neighbours, b over its four face neighbours.  Stored as {E_x,E_y,E_z,B_x} and {B_y,B_z}.
+__global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nfA, float2 *nfB) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
         int pi, pj, pk;
@@ -166,8 +197,8 @@ __global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nf) {
                         sval(g, f.b[1], true, i, j, k - 1) + sval(g, f.b[1], true, i - 1, j, k - 1));
         B[2] = 0.25f * (sval(g, f.b[2], true, i, j, k) + sval(g, f.b[2], true, i - 1, j, k) +
                         sval(g, f.b[2], true, i - 1, j - 1, k) + sval(g, f.b[2], true, i, j - 1, k));
-        nf[2 * p] = make_float4(E[0], E[1], E[2], B[0]);
-        nf[2 * p + 1] = make_float4(B[1], B[2], 0.f, 0.f);
+        nfA[p] = make_float4(E[0], E[1], E[2], B[0]);
+        nfB[p] = make_float2(B[1], B[2]);
     }
 }
 
@@ -205,8 +236,14 @@ void launch_e_advance(const Geom &g, FieldPtrs<R> f, const R *const J[3], R *con
                                                            dt);
 }
 
-void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nf, cudaStream_t s) {
-    k_node_fields<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, nf);
+void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nfA, float2 *nfB, cudaStream_t s) {
+    k_node_fields<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, nfA, nfB);
+}
+
+void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long long *const J[3],
+                         unsigned long long *const Jzero[3], float dt, double alpha_abs, cudaStream_t s) {
+    k_e_advance_fx<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, J[0], J[1], J[2], Jzero[0], Jzero[1], Jzero[2],
+                                                           dt, alpha_abs * 0x1p-36);
 }
 
 template <typename R>

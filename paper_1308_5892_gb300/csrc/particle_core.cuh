@@ -1,7 +1,8 @@
 // particle_core.cuh -- per-particle arithmetic shared by the FP64 and the
 // mixed-precision push kernels: the relativistic Boris step (App. A.3.3) and
-// the charge-conserving current of one straight segment inside one cell
-// (App. A.1, A.3.4, Eq. current_dep).
+// the charge-conserving current of straight segments inside one cell (App.
+// A.1, A.3.4, Eq. current_dep).  Everything is written with compile-time
+// indices only, so no per-thread array spills to local memory.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -32,28 +33,29 @@ __device__ inline void boris(R u[3], const R E[3], const R B[3], R h, R dt) {
     u[2] = um[2] + (up[0] * s[1] - up[1] * s[0]) + qe * E[2];
 }
 
-// Current of one straight segment inside cell (ci, cj, ck): the particle (a
-// cube of volume 1) starts at offset d within the cell and moves by D.  With
+// Current of one straight segment inside one cell: the particle (a cube of
+// volume 1) starts at offset d within the cell and moves by D.  With
 // mid-point weights W^0 = 1 - (d + D/2), W^1 = d + D/2, the flux through the x
 // face at (i+1/2, j+eta, k+xi) is D_x [W_y^eta W_z^xi + (-1)^(eta+xi) D_y D_z/12]
-// (the exact time integral of the overlap area), and enters Ampere's law as
-// -alpha times that flux; y and z by cyclic permutation.  In 2D3V the cube is
-// uniform along z: in-plane fluxes D_x W_y^eta and D_y W_x^eps, and the
-// out-of-plane flux D_z [W_x^eps W_y^eta + (-1)^(eps+eta) D_x D_y / 12] goes to
-// e_z at node (i+eps, j+eta).  sink(comp, di, dj, dk, value) receives -alpha F
-// for the current component comp at cell offset (di,dj,dk) from (ci,cj,ck).
+// (the exact time integral of the overlap area of the cube with the face), and
+// enters Ampere's law as -alpha times that flux; y and z by cyclic permutation.
+// In 2D3V the cube is uniform along z: in-plane fluxes D_x W_y^eta and
+// D_y W_x^eps, and the out-of-plane flux D_z [W_x^eps W_y^eta + (-1)^(eps+eta)
+// D_x D_y / 12] goes to e_z at node (i+eps, j+eta).
+// sink(comp, di, dj, dk, value) receives -alpha F for current component comp
+// at offset (di, dj, dk) from the segment's cell (set by sink.set_cell).
 template <int NDIM, typename R, class Sink>
-__device__ inline void deposit_segment(const R d[3], const R D[3], R alpha, Sink &sink) {
+__device__ __forceinline__ void deposit_segment(const R d[3], const R D[3], R alpha, Sink &sink) {
     R w1[3], w0[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         w1[a] = d[a] + R(0.5) * D[a];
         w0[a] = R(1) - w1[a];
     }
+    const R ax = -alpha * D[0], ay = -alpha * D[1], az = -alpha * D[2];
     if (NDIM == 3) {
         const R cyz = D[1] * D[2] * R(1.0 / 12.0), czx = D[2] * D[0] * R(1.0 / 12.0),
                 cxy = D[0] * D[1] * R(1.0 / 12.0);
-        const R ax = -alpha * D[0], ay = -alpha * D[1], az = -alpha * D[2];
         // x faces (i+1/2, j+p, k+q)
         sink(0, 0, 0, 0, ax * (w0[1] * w0[2] + cyz));
         sink(0, 0, 1, 0, ax * (w1[1] * w0[2] - cyz));
@@ -70,7 +72,6 @@ __device__ inline void deposit_segment(const R d[3], const R D[3], R alpha, Sink
         sink(2, 0, 1, 0, az * (w0[0] * w1[1] - cxy));
         sink(2, 1, 1, 0, az * (w1[0] * w1[1] + cxy));
     } else {
-        const R ax = -alpha * D[0], ay = -alpha * D[1], az = -alpha * D[2];
         const R cxy = D[0] * D[1] * R(1.0 / 12.0);
         sink(0, 0, 0, 0, ax * w0[1]);
         sink(0, 0, 1, 0, ax * w1[1]);
@@ -84,66 +85,93 @@ __device__ inline void deposit_segment(const R d[3], const R D[3], R alpha, Sink
 }
 
 // Straight path from offset d0 in the start cell to the stored end: per axis a,
-// shift s[a] in {-1,0,1} cells and end offset d1[a] in the end cell.  The path
-// is split at the node planes it crosses (at most one per axis), segments in
-// increasing crossing parameter, ties in axis order; each piece is deposited
-// in its own cell by deposit_segment.  Positions at the breakpoints are taken
-// from the stored values (plane, stored end) so the segment displacements
-// telescope to the stored total and charge is conserved to rounding of the
-// fluxes.  dz2d is the out-of-plane displacement in 2D3V, shared between the
-// segments in proportion to their parameter length.  cell_sink(di,dj,dk)
-// re-targets the sink to the segment's cell (offset from the start cell).
+// a shift s[a] in {-1,0,1} cells and the end offset d1[a] in the end cell.  The
+// path is split at the node planes it crosses (at most one per axis); the
+// pieces are taken in increasing crossing parameter, ties in axis order, and
+// each piece is deposited in its own cell by deposit_segment.  Positions at
+// the breakpoints are the exact plane values and the stored end, so the
+// segment displacements telescope to the stored total and charge is conserved
+// up to the rounding of the fluxes.  dz2d is the out-of-plane displacement in
+// 2D3V, shared between the pieces in proportion to their parameter length.
+// sink.piece(k, di, dj, dk, d, D, alpha) receives piece k, its cell offset from
+// the start cell, its start offset d and displacement D; PieceDeposit below
+// deposits it at once.
 template <int NDIM, typename R, class Sink>
-__device__ inline void deposit_path(const R d0[3], const int s[3], const R d1[3], R dz2d, R alpha, Sink &sink) {
+__device__ __forceinline__ void deposit_path(const R d0[3], const int s[3], const R d1[3], R dz2d, R alpha,
+                                             Sink &sink) {
     R tc[3], dv[3], plo[3], pnew[3];
-    bool crossed[3] = {false, false, false};
     int ncross = 0;
 #pragma unroll
-    for (int a = 0; a < NDIM; ++a) {
-        plo[a] = s[a] > 0 ? R(1) : R(0);   // crossing plane in start-cell coordinates
-        pnew[a] = s[a] > 0 ? R(0) : R(1);  // the same plane in end-cell coordinates
-        if (s[a] != 0) {
-            const R first = plo[a] - d0[a];
-            const R second = d1[a] - pnew[a];
-            dv[a] = first + second;
-            tc[a] = dv[a] != R(0) ? first / dv[a] : R(0);
-            ++ncross;
-        } else {
-            dv[a] = d1[a] - d0[a];
-            tc[a] = R(2);
+    for (int a = 0; a < 3; ++a) {
+        tc[a] = R(2);
+        dv[a] = R(0);
+        plo[a] = R(0);
+        pnew[a] = R(0);
+        if (a < NDIM) {
+            plo[a] = s[a] > 0 ? R(1) : R(0);   // crossing plane in start-cell coordinates
+            pnew[a] = s[a] > 0 ? R(0) : R(1);  // the same plane in end-cell coordinates
+            if (s[a] != 0) {
+                const R first = plo[a] - d0[a];
+                dv[a] = first + (d1[a] - pnew[a]);
+                tc[a] = dv[a] != R(0) ? first / dv[a] : R(0);
+                ++ncross;
+            } else {
+                dv[a] = d1[a] - d0[a];
+            }
         }
+    }
+    // rank of each axis' crossing (non-crossing axes rank last), ties by axis order
+    int rank[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        rank[a] = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            if (b != a && b < NDIM && a < NDIM && (tc[b] < tc[a] || (tc[b] == tc[a] && b < a))) ++rank[a];
     }
     R cur[3] = {d0[0], d0[1], NDIM == 3 ? d0[2] : R(0)};
     int cs[3] = {0, 0, 0};
     R tprev = R(0);
-    for (int seg = 0; seg <= ncross; ++seg) {
-        // next crossing: smallest tc among axes not yet crossed (ties: lowest axis)
-        int ax = -1;
+    // one rolled loop over the pieces keeps a single copy of the deposit in the
+    // instruction stream; every array below is still indexed by unrolled axes
+#pragma unroll 1
+    for (int k = 0; k <= ncross; ++k) {
         R tn = R(1);
 #pragma unroll
         for (int a = 0; a < NDIM; ++a)
-            if (s[a] != 0 && !crossed[a] && (ax < 0 || tc[a] < tn)) { ax = a; tn = tc[a]; }
-        if (ax < 0) tn = R(1);
+            if (s[a] != 0 && rank[a] == k) tn = tc[a];
+        const bool last = (k == ncross);
         R D[3], endp[3];
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            if (a == ax) endp[a] = plo[a];
-            else if (ax < 0) endp[a] = d1[a];
-            else if (crossed[a]) endp[a] = pnew[a] + dv[a] * (tn - tc[a]);
+        for (int a = 0; a < 3; ++a) {
+            if (a >= NDIM) { endp[a] = R(0); D[a] = R(0); continue; }
+            const bool cx = s[a] != 0;
+            if (cx && rank[a] == k) endp[a] = plo[a];
+            else if (last) endp[a] = d1[a];
+            else if (cx && rank[a] < k) endp[a] = pnew[a] + dv[a] * (tn - tc[a]);
             else endp[a] = d0[a] + dv[a] * tn;
             D[a] = endp[a] - cur[a];
         }
-        if (NDIM == 2) { D[2] = dz2d * (tn - tprev); cur[2] = R(0); }
-        sink.set_cell(cs[0], cs[1], cs[2]);
-        deposit_segment<NDIM, R>(cur, D, alpha, sink);
+        if (NDIM == 2) D[2] = dz2d * (tn - tprev);
+        sink.piece(k, cs[0], cs[1], cs[2], cur, D, alpha);
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) cur[a] = endp[a];
-        if (ax < 0) break;
-        cur[ax] = pnew[ax];
-        cs[ax] = s[ax];
-        crossed[ax] = true;
+        for (int a = 0; a < NDIM; ++a) {
+            cur[a] = endp[a];
+            if (s[a] != 0 && rank[a] == k) { cur[a] = pnew[a]; cs[a] = s[a]; }
+        }
         tprev = tn;
     }
 }
+
+// Adapter: a value sink (set_cell + operator()) that deposits every piece at once.
+template <int NDIM, typename R, class ValueSink>
+struct PieceDeposit {
+    ValueSink &vs;
+    __device__ __forceinline__ explicit PieceDeposit(ValueSink &v) : vs(v) {}
+    __device__ __forceinline__ void piece(int, int di, int dj, int dk, const R d[3], const R D[3], R alpha) {
+        vs.set_cell(di, dj, dk);
+        deposit_segment<NDIM, R>(d, D, alpha, vs);
+    }
+};
 
 }  // namespace pic

@@ -91,7 +91,10 @@ void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, double *energy_acc, cu
 template <typename R>
 void launch_e_advance(const Geom &g, FieldPtrs<R> f, const R *const J[3], R *const Jzero[3], R dt,
                       cudaStream_t s);
-void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nf, cudaStream_t s);
+void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nfA, float2 *nfB, cudaStream_t s);
+// e += dt curl b + |alpha| * J for the fixed-point current of the mixed path
+void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long long *const J[3],
+                         unsigned long long *const Jzero[3], float dt, double alpha_abs, cudaStream_t s);
 template <typename R>
 void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s);
 
@@ -104,17 +107,23 @@ void launch_push_fp64(const Geom &g, FieldPtrs<double> f, double *const J[3], Sp
 struct MixedStepArgs {
     Geom g;
     TileGeom t;
-    const float4 *nf;          // node fields (padded, 2 float4 per cell)
-    float *J[3];               // padded current planes being accumulated
-    SpeciesMixed sp;
-    const int *tile_start;     // ntiles+1 offsets into the particle arrays
-    float h, alpha, dt;
-    int mode;                  // 0 step, 1 half step back (momenta only)
-    double *kin_acc;           // 2 doubles: kinetic energy of u^{t-1/2} and u^{t+1/2} (times m/m_e)
-    double m_over_me;
+    const float4 *nfA;              // node fields {E_x,E_y,E_z,B_x} per padded cell
+    const float2 *nfB;              // node fields {B_y,B_z} per padded cell
+    unsigned long long *J[3];       // padded int64 fixed-point current planes (units 2^-36 of sgn(q) flux)
+    int nspecies;
+    SpeciesMixed sp[4];
+    const int *tile_start[4];       // per species: ntiles+1 offsets into the particle arrays
+    float h[4];                     // (q/e)(m_e/m)
+    float sgn[4];                   // sign of the charge
+    double m_over_me[4];
+    float dt;
+    int mode;                       // 0 step, 1 half step back (momenta only)
+    double *kin_acc;                // 2 doubles: kinetic energy of u^{t-1/2} and u^{t+1/2}
     int *err;
 };
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
+void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
+                            float h, float dt, cudaStream_t s);
 size_t mixed_smem_bytes(const TileGeom &t, int ndim);
 
 // sort.cu
@@ -127,6 +136,7 @@ struct SortArgs {
     int *offsets;    // same size: exclusive scan; offsets[key] start of key
     int *block_sums; // scratch for the scan
     int *tile_start; // ntiles+1 output
+    int *perm;       // n scratch: source index of every destination slot
     int *err;
 };
 void launch_sort(const SortArgs &a, cudaStream_t s);

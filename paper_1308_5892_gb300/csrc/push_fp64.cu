@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(256) k_push_fp64(Geom g, FieldPtrs<double> f, 
                 endabs[a] = (double)(c0[a] + s[a]) + da;
             }
             sink.ci = c0[0]; sink.cj = c0[1]; sink.ck = NDIM == 3 ? c0[2] : 0;
-            deposit_path<NDIM, double>(d0, s, d1, dleg[leg][2], alpha, sink);
+            PieceDeposit<NDIM, double, GlobalSink64> pd(sink);
+            deposit_path<NDIM, double>(d0, s, d1, dleg[leg][2], alpha, pd);
         }
         // store: periodic wrap into [0, n)
         double xo = endabs[0];

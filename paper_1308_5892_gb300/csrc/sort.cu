@@ -1,14 +1,19 @@
 // sort.cu -- counting sort of the mixed-path particles by tile-major cell key.
 //
 // key(cell) = tile_index * cells_per_tile + index of the cell inside its tile,
-// so particles end up grouped by tile and, inside a tile, by cell.  The sort
+// so particles end up grouped by tile and, inside a tile, by cell; the cell
+// order inside a tile is then stored block-transposed (interleaved_slot).  The sort
 // is out of place (src -> dst, the caller swaps the buffers): histogram of the
-// keys, exclusive scan, and a scatter whose per-key cursors are advanced with
+// keys, exclusive scan, a rank pass whose per-key cursors are advanced with
 // warp-aggregated atomics (lanes of a warp that share a key take consecutive
-// slots with one atomic).  The tile offsets are read from the scanned counts.
+// slots with one atomic) and which writes only the 4-byte inverse permutation,
+// then a gather pass that writes every particle array in destination order
+// (coalesced stores; scattered partial-sector stores of the full particle
+// state cost several times its size in DRAM traffic).  The tile offsets are
+// read from the scanned counts.
 //
-// Roofline: HBM bound; per particle 4 B (histogram) + 2 x (24..28 + 4) B
-// (scatter) plus per key 3 x 4 B.
+// Roofline: HBM bound; per particle 4 B (histogram) + 8 B (rank) +
+// 4 + 2 x (24..28 + 4) B (gather) plus per key 3 x 4 B.
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -122,11 +127,25 @@ __global__ void k_scan_finish(int *offsets, int *cursors, const int *block_sums,
     if (blockIdx.x == 0 && threadIdx.x == 0) tile_start[ntiles] = (int)n;
 }
 
+// Position of cell-sorted rank r inside a tile of n_t particles: every full
+// block of 1024 is stored as a 32 x 32 transpose, so that lane a of a warp,
+// reading element base + 32k + a for k = 0..31, walks the 32 consecutive
+// ranks 32a .. 32a+31 (mostly one cell) while the 32 lanes of one load sit in
+// 32 different cells; the tail of the tile (n_t mod 1024) keeps rank order.
+__device__ __forceinline__ int interleaved_slot(int r, int n_t) {
+    const int nfull = n_t & ~1023;
+    if (r >= nfull) return r;
+    const int i = r & 1023;
+    return (r - i) + ((i & 31) << 5) + (i >> 5);
+}
+
+// Rank pass: the destination slot of every source particle, written as the
+// inverse permutation perm[slot] = source index (4-byte scattered writes only).
 template <int NDIM>
-__global__ void k_scatter(TileGeom t, SpeciesMixed src, SpeciesMixed dst, long long n, int *cursors, long long nkeys) {
+__global__ void k_rank(TileGeom t, const uint32_t *cell, long long n, int *cursors, long long nkeys,
+                       const int *tile_start, int *perm) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const uint32_t c = src.cell[p];
-        const int key = cell_key<NDIM>(t, c);
+        const int key = cell_key<NDIM>(t, cell[p]);
         if (key < 0 || key >= nkeys) continue;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, key);
@@ -135,15 +154,26 @@ __global__ void k_scatter(TileGeom t, SpeciesMixed src, SpeciesMixed dst, long l
         int base = 0;
         if (lane == leader) base = atomicAdd(cursors + key, __popc(peers));
         base = __shfl_sync(peers, base, leader);
-        const int q = base + __popc(peers & ((1u << lane) - 1u));
-        dst.cell[q] = c;
-        dst.off[0][q] = src.off[0][p];
-        dst.off[1][q] = src.off[1][p];
-        if (NDIM == 3) dst.off[2][q] = src.off[2][p];
-        dst.u[0][q] = src.u[0][p];
-        dst.u[1][q] = src.u[1][p];
-        dst.u[2][q] = src.u[2][p];
-        dst.id[q] = src.id[p];
+        const int rank = base + __popc(peers & ((1u << lane) - 1u));
+        const int tile = key / t.cells_per_tile;
+        const int t0 = tile_start[tile], t1 = tile_start[tile + 1];
+        perm[t0 + interleaved_slot(rank - t0, t1 - t0)] = (int)p;
+    }
+}
+
+// Gather pass in destination order: coalesced writes, reads through L2.
+template <int NDIM>
+__global__ void k_gather(SpeciesMixed src, SpeciesMixed dst, long long n, const int *perm) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int p = perm[q];
+        dst.cell[q] = __ldg(src.cell + p);
+        dst.off[0][q] = __ldg(src.off[0] + p);
+        dst.off[1][q] = __ldg(src.off[1] + p);
+        if (NDIM == 3) dst.off[2][q] = __ldg(src.off[2] + p);
+        dst.u[0][q] = __ldg(src.u[0] + p);
+        dst.u[1][q] = __ldg(src.u[1] + p);
+        dst.u[2][q] = __ldg(src.u[2] + p);
+        dst.id[q] = __ldg(src.id + p);
     }
 }
 
@@ -170,8 +200,13 @@ void launch_sort(const SortArgs &a, cudaStream_t s) {
     k_scan_finish<<<blocks_for(nkeys, 256), 256, 0, s>>>(a.offsets, a.counts, a.block_sums, nkeys,
                                                          a.t.cells_per_tile, a.t.ntiles, a.tile_start, a.n);
     if (a.n > 0) {
-        if (a.g.ndim == 3) k_scatter<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src, a.dst, a.n, a.counts, nkeys);
-        else k_scatter<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src, a.dst, a.n, a.counts, nkeys);
+        if (a.g.ndim == 3) {
+            k_rank<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.tile_start, a.perm);
+            k_gather<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.src, a.dst, a.n, a.perm);
+        } else {
+            k_rank<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.tile_start, a.perm);
+            k_gather<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.src, a.dst, a.n, a.perm);
+        }
     }
 }
 

@@ -40,11 +40,15 @@ def _oracle_state(desc, fields, parts, arr):
 
 
 def _rel(a, b):
+    if a.size == 0:
+        return 0.0
     den = np.abs(b).max()
     return np.abs(a - b).max() / den if den > 0 else np.abs(a - b).max()
 
 
 def _pos_diff(a, b, L):
+    if a.size == 0:
+        return 0.0
     d = a - b
     return np.abs(d - L * np.round(d / L)).max()
 
