@@ -29,7 +29,9 @@ struct SpeciesState {
     Species64 s64{};            // FP64 path
     SpeciesMixed mb[2]{};       // mixed path: current and sort target
     int cur = 0;
-    int *tile_start = nullptr;  // ntiles + 1
+    int *tile_start = nullptr;  // ntiles + 1, offsets of the current layout
+    int *tile_start_alt = nullptr;
+    bool tiled = false;         // current layout comes from a sort
 };
 
 struct Run {
@@ -298,7 +300,7 @@ void choose_tiles(Run &r, const pic_opts *o) {
     }
     r.t.ntiles = r.t.ntile[0] * r.t.ntile[1] * r.t.ntile[2];
     r.t.cells_per_tile = T[0] * T[1] * T[2];
-    r.sort_interval = (o && o->sort_interval > 0) ? o->sort_interval : (d.ndim == 2 ? 4 : 2);
+    r.sort_interval = (o && o->sort_interval > 0) ? o->sort_interval : (d.ndim == 2 ? 8 : 2);
 }
 
 pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
@@ -370,7 +372,8 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
                 if (!m.cell || !m.id) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for particles");
             }
             S.tile_start = (int *)dev_alloc(ctx, sizeof(int) * (r.t.ntiles + 1));
-            if (!S.tile_start) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for tile offsets");
+            S.tile_start_alt = (int *)dev_alloc(ctx, sizeof(int) * (r.t.ntiles + 1));
+            if (!S.tile_start || !S.tile_start_alt) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for tile offsets");
             CK(cudaMemsetAsync(S.tile_start, 0, sizeof(int) * (r.t.ntiles + 1), ctx->stream));
         }
     }
@@ -409,11 +412,14 @@ void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
     a.counts = r.counts;
     a.offsets = r.offsets;
     a.block_sums = r.block_sums;
-    a.tile_start = S.tile_start;
+    a.old_tile_start = S.tiled ? S.tile_start : nullptr;
+    a.tile_start = S.tile_start_alt;
     a.perm = r.perm;
     a.err = ctx->d_err;
     launch_sort(a, ctx->stream);
     S.cur = 1 - S.cur;
+    std::swap(S.tile_start, S.tile_start_alt);
+    S.tiled = true;
 }
 
 void step_run(pic_ctx *ctx, Run &r) {
@@ -620,6 +626,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
             }
         } else {
             S.cur = 0;
+            S.tiled = false;
             const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
             for (int64_t a0 = 0; a0 < n; a0 += chunk) {
                 const int64_t m = std::min(chunk, n - a0);

@@ -136,6 +136,7 @@ struct SortArgs {
     int *offsets;    // same size: exclusive scan; offsets[key] start of key
     int *block_sums; // scratch for the scan
     int *tile_start; // ntiles+1 output
+    const int *old_tile_start;  // tile offsets of the source layout, or nullptr if untiled
     int *perm;       // n scratch: source index of every destination slot
     int *err;
 };

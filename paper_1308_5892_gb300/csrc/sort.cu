@@ -34,14 +34,59 @@ __device__ inline int cell_key(const TileGeom &t, uint32_t c) {
     return tile * t.cells_per_tile + (lk * t.T[1] + lj) * t.T[0] + li;
 }
 
+// Position of cell-sorted rank r inside a tile of n_t particles: every full
+// block of 1024 is stored as a 32 x 32 transpose, so that lane a of a warp,
+// reading element base + 32k + a for k = 0..31, walks the 32 consecutive
+// ranks 32a .. 32a+31 (mostly one cell) while the 32 lanes of one load sit in
+// 32 different cells; the tail of the tile (n_t mod 1024) keeps rank order.
+__device__ __forceinline__ int interleaved_slot(int r, int n_t) {
+    const int nfull = n_t & ~1023;
+    if (r >= nfull) return r;
+    const int i = r & 1023;
+    return (r - i) + ((i & 31) << 5) + (i >> 5);
+}
+
+// Source traversal: with a tiled source (sorted before), CTA b walks old tile b
+// in its cell-sorted rank order (slot t0 + interleaved_slot(i)), so consecutive
+// threads see consecutive ranks of one cell; an untiled source (as uploaded)
+// is walked in storage order by a grid-stride loop.
+struct SrcWalk {
+    const int *old_start;   // old tile offsets, or nullptr when the source is untiled
+    long long n;
+    __device__ __forceinline__ bool begin(long long &i, long long &end, int &t0, int &nt) const {
+        if (old_start) {
+            t0 = old_start[blockIdx.x];
+            nt = old_start[blockIdx.x + 1] - t0;
+            i = threadIdx.x;
+            end = nt;
+        } else {
+            t0 = 0;
+            nt = 0;
+            i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+            end = n;
+        }
+        return true;
+    }
+    __device__ __forceinline__ long long step() const {
+        return old_start ? (long long)blockDim.x : (long long)gridDim.x * blockDim.x;
+    }
+    __device__ __forceinline__ long long pos(long long i, int t0, int nt) const {
+        return old_start ? (long long)t0 + interleaved_slot((int)i, nt) : i;
+    }
+};
+
 __global__ void k_zero(int *a, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] = 0;
 }
 
 template <int NDIM>
-__global__ void k_histogram(TileGeom t, const uint32_t *cell, long long n, int *counts, long long nkeys, int *err) {
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+__global__ void k_histogram(TileGeom t, const uint32_t *cell, SrcWalk w, int *counts, long long nkeys, int *err) {
+    long long i, end;
+    int t0, nt;
+    w.begin(i, end, t0, nt);
+    for (; i < end; i += w.step()) {
+        const long long p = w.pos(i, t0, nt);
         const int key = cell_key<NDIM>(t, cell[p]);
         if (key < 0 || key >= nkeys) { atomicOr(err, ERR_SORT); continue; }
         // warp aggregation: lanes with the same key add once
@@ -127,24 +172,16 @@ __global__ void k_scan_finish(int *offsets, int *cursors, const int *block_sums,
     if (blockIdx.x == 0 && threadIdx.x == 0) tile_start[ntiles] = (int)n;
 }
 
-// Position of cell-sorted rank r inside a tile of n_t particles: every full
-// block of 1024 is stored as a 32 x 32 transpose, so that lane a of a warp,
-// reading element base + 32k + a for k = 0..31, walks the 32 consecutive
-// ranks 32a .. 32a+31 (mostly one cell) while the 32 lanes of one load sit in
-// 32 different cells; the tail of the tile (n_t mod 1024) keeps rank order.
-__device__ __forceinline__ int interleaved_slot(int r, int n_t) {
-    const int nfull = n_t & ~1023;
-    if (r >= nfull) return r;
-    const int i = r & 1023;
-    return (r - i) + ((i & 31) << 5) + (i >> 5);
-}
-
 // Rank pass: the destination slot of every source particle, written as the
 // inverse permutation perm[slot] = source index (4-byte scattered writes only).
 template <int NDIM>
-__global__ void k_rank(TileGeom t, const uint32_t *cell, long long n, int *cursors, long long nkeys,
+__global__ void k_rank(TileGeom t, const uint32_t *cell, SrcWalk w, int *cursors, long long nkeys,
                        const int *tile_start, int *perm) {
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    long long i, end;
+    int t0s, nts;
+    w.begin(i, end, t0s, nts);
+    for (; i < end; i += w.step()) {
+        const long long p = w.pos(i, t0s, nts);
         const int key = cell_key<NDIM>(t, cell[p]);
         if (key < 0 || key >= nkeys) continue;
         const unsigned act = __activemask();
@@ -189,10 +226,14 @@ size_t sort_scan_scratch(long long nkeys) { return (size_t)((nkeys + kScanTile -
 
 void launch_sort(const SortArgs &a, cudaStream_t s) {
     const long long nkeys = (long long)a.t.ntiles * a.t.cells_per_tile;
+    SrcWalk w;
+    w.old_start = a.old_tile_start;
+    w.n = a.n;
+    const int wblocks = a.old_tile_start ? a.t.ntiles : blocks_for(a.n, 256);
     k_zero<<<blocks_for(nkeys, 256), 256, 0, s>>>(a.counts, nkeys);
     if (a.n > 0) {
-        if (a.g.ndim == 3) k_histogram<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.err);
-        else k_histogram<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.err);
+        if (a.g.ndim == 3) k_histogram<3><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.err);
+        else k_histogram<2><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.err);
     }
     const int nb = (int)((nkeys + kScanTile - 1) / kScanTile);
     k_scan_blocks<<<nb, kScanThreads, 0, s>>>(a.counts, a.offsets, a.block_sums, nkeys);
@@ -201,10 +242,10 @@ void launch_sort(const SortArgs &a, cudaStream_t s) {
                                                          a.t.cells_per_tile, a.t.ntiles, a.tile_start, a.n);
     if (a.n > 0) {
         if (a.g.ndim == 3) {
-            k_rank<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.tile_start, a.perm);
+            k_rank<3><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.tile_start, a.perm);
             k_gather<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.src, a.dst, a.n, a.perm);
         } else {
-            k_rank<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.t, a.src.cell, a.n, a.counts, nkeys, a.tile_start, a.perm);
+            k_rank<2><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.tile_start, a.perm);
             k_gather<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.src, a.dst, a.n, a.perm);
         }
     }
