@@ -1,0 +1,31 @@
+"""Closed-form relations of the paper used as physics pins (TEST INFRASTRUCTURE).
+
+- Relativistic Harris sheet (App. C, Eq. velocity_Harris and Eq. pressure_ad)
+  for a pair plasma with equal temperatures (chi = 1): Theta = (omega_ce /
+  omega'_pe)^2 / 4 and Gamma U / c = 2 Theta (d'_e / L)(omega'_pe / omega_ce);
+  lab-frame plasma frequency omega_pe = sqrt(Gamma) omega'_pe (Sect. 3.4).
+- Cold filamentation growth time for k_perp -> infinity (Sect. 3.2.1):
+  tau = (1/2 pi) sqrt(Gamma0 / 2) / beta0 T_pe for pair beams.  The same cold
+  two-fluid limit, delta^2 = sum_s omega_ps^2 beta_s^2 / gamma_s over the beam
+  populations, gives tau = (1/2 pi) sqrt(Gamma0) / beta0 T_pe for two electron
+  beams of half density each on a positron background at rest.
+"""
+import numpy as np
+
+
+def harris_from_theta_GU(theta, GU):
+    """(omega_ce/omega_pe, L/d_e) in lab-frame units from Theta and Gamma_e U_e / c."""
+    G = np.sqrt(1.0 + GU * GU)
+    wce_over_wpe_prime = 2.0 * np.sqrt(theta)        # pressure balance, chi = 1
+    L_over_dprime = 2.0 * theta / (GU * wce_over_wpe_prime)
+    return wce_over_wpe_prime / np.sqrt(G), L_over_dprime * np.sqrt(G)
+
+
+def tau_filamentation_pair(beta0):
+    G0 = 1.0 / np.sqrt(1.0 - beta0 * beta0)
+    return np.sqrt(G0 / 2.0) / beta0 / (2.0 * np.pi)
+
+
+def tau_filamentation_electron_beams(beta0):
+    G0 = 1.0 / np.sqrt(1.0 - beta0 * beta0)
+    return np.sqrt(G0) / beta0 / (2.0 * np.pi)
