@@ -16,8 +16,8 @@
  *  - Host pointers are borrowed for the duration of the call only.
  *  - Device memory belongs to the context.  It is obtained through the
  *    caller's pic_allocator (or cudaMalloc when none is given) inside
- *    pic_init and returned in pic_destroy; no other call allocates, except
- *    the loader's temporary lookup table (freed before it returns).
+ *    pic_init and returned in pic_destroy; no other call allocates device
+ *    memory.
  *  - Device work is queued on the stream given in pic_opts (NULL: the legacy
  *    default stream).  Calls that return data to the host synchronise that
  *    stream; pic_step synchronises it unless PIC_FLAG_ASYNC is set.
@@ -183,8 +183,14 @@ const char *pic_last_error(const pic_ctx *ctx);
  * not exceed the capacities.  Non-finite values give PIC_ENUMERIC. */
 pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in);
 
-/* Download the state into caller buffers (converted to FP64). */
+/* Download the state into caller buffers (converted to FP64).  A NULL
+ * particles[s] skips species s (count[s] still receives its size). */
 pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out);
+
+/* Copy chosen particles of one species by id (ids as returned in load/set
+ * order, 0 <= id < count): out holds 6 * nids doubles, planes x, y, z, u_x,
+ * u_y, u_z, in the order of ids.  Synchronises. */
+pic_status pic_get_particles(pic_ctx *ctx, int run, int species, const int64_t *ids, int64_t nids, double *out);
 
 /* Add uniform fields e0 to e and b0 to b of one run (tests; background field). */
 pic_status pic_set_uniform_field(pic_ctx *ctx, int run, const double e0[3], const double b0[3]);

@@ -27,7 +27,7 @@ MAX_SPECIES = 4
 ABI_FUNCTIONS = [
     "pic_abi_version", "pic_init", "pic_destroy", "pic_last_error", "pic_set_state", "pic_get_state",
     "pic_set_uniform_field", "pic_load_maxwell_juttner", "pic_step", "pic_sync", "pic_diagnostics",
-    "pic_energy_history", "pic_get_tuning", "pic_get_counters", "pic_kernel_time",
+    "pic_energy_history", "pic_get_tuning", "pic_get_counters", "pic_kernel_time", "pic_get_particles",
 ]
 
 
@@ -113,6 +113,8 @@ def lib(build_if_missing=True):
         "pic_get_counters": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], st),
         "pic_kernel_time": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int64)], st),
+        "pic_get_particles": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_double)], st),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -221,7 +223,7 @@ class Context:
             v.particles[s] = _dptr(p)
         return self._check(self._L.pic_set_state(self.h, run, ctypes.byref(v)))
 
-    def get_state(self, run, out=None):
+    def get_state(self, run, out=None, fields_only=False):
         d = self.runs[run]
         nz = 1 if d.ndim == 2 else d.nz
         fields = np.zeros((6, nz, d.ny, d.nx)) if out is None else out[0]
@@ -229,11 +231,16 @@ class Context:
         v.fields = _dptr(fields)
         parts = []
         for s in range(d.nspecies):
+            if fields_only:
+                parts.append(None)
+                continue
             p = np.zeros((6, int(d.species[s].capacity))) if out is None else out[1][s]
             parts.append(p)
             v.count[s] = p.shape[1]
             v.particles[s] = _dptr(p)
         self._check(self._L.pic_get_state(self.h, run, ctypes.byref(v)))
+        if fields_only:
+            return fields, [int(v.count[s]) for s in range(d.nspecies)], v.step
         res = []
         for s in range(d.nspecies):
             n = v.count[s]
@@ -303,3 +310,11 @@ class Context:
         n = ctypes.c_int64()
         self._check(self._L.pic_kernel_time(self.h, kernel_class, int(reset), ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def get_particles(self, run, species, ids):
+        """Particles of one species by id: (6, len(ids)) planes x, y, z, u_x, u_y, u_z."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        out = np.zeros((6, len(ids)))
+        self._check(self._L.pic_get_particles(self.h, run, species, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                              len(ids), _dptr(out)))
+        return out

@@ -69,6 +69,7 @@ struct pic_ctx {
     int *d_err = nullptr;
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    double *mj_table = nullptr;     // cumulative marginal of the loader, kMjTable + 1 values
     std::vector<std::pair<void *, size_t>> allocs;
     std::string err;
     int64_t launches_per_step = 0;
@@ -212,6 +213,36 @@ __global__ void k_upload_mixed(Geom g, const double *st, long long m, long long 
         d.u[1][a + q] = (float)st[4 * m + q];
         d.u[2][a + q] = (float)st[5 * m + q];
         d.id[a + q] = (int32_t)(a + q);
+    }
+}
+
+// inverse map id -> storage index, then gather of the requested ids
+__global__ void k_id_index(const int32_t *id, long long n, int *inv) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        inv[id[p]] = (int)p;
+}
+
+__global__ void k_pick_mixed(Geom g, SpeciesMixed s, const int *inv, const long long *ids, long long m, double *st) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        const int p = inv[ids[q]];
+        int i, j, k;
+        unpack_cell(g.ndim, s.cell[p], i, j, k);
+        st[q] = (double)i + (double)s.off[0][p];
+        st[m + q] = (double)j + (double)s.off[1][p];
+        st[2 * m + q] = g.ndim == 3 ? (double)k + (double)s.off[2][p] : 0.0;
+        st[3 * m + q] = s.u[0][p];
+        st[4 * m + q] = s.u[1][p];
+        st[5 * m + q] = s.u[2][p];
+    }
+}
+
+__global__ void k_pick64(Species64 s, const long long *ids, long long m, int ndim, double *st) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        const long long p = ids[q];
+        for (int c = 0; c < 3; ++c) {
+            st[c * m + q] = (c < ndim) ? s.x[c][p] : 0.0;
+            st[(3 + c) * m + q] = s.u[c][p];
+        }
     }
 }
 
@@ -509,6 +540,9 @@ void step_run(pic_ctx *ctx, Run &r) {
 
 }  // namespace
 
+pic_status mlp_load(pic_ctx *ctx, int run, int species, long long n, double theta, const double beta[3], int profile,
+                    double L, double x0, int colocate_with, uint64_t seed);
+
 // ================================================================== ABI
 
 extern "C" {
@@ -548,9 +582,11 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
         for (int s = 0; s < runs[r].nspecies; ++s) cap = std::max<int64_t>(cap, runs[r].species[s].capacity);
         stage = std::max(stage, 6 * sizeof(double) * (size_t)std::min<int64_t>(cap, 1 << 24));
     }
+    stage = std::max<size_t>(stage, 1 << 16);
     ctx->staging_bytes = stage;
     ctx->staging = dev_alloc(ctx, stage);
-    if (!ctx->staging) { pic_destroy(ctx); return PIC_ENOMEM; }
+    ctx->mj_table = (double *)dev_alloc(ctx, sizeof(double) * (kMjTable + 1));
+    if (!ctx->staging || !ctx->mj_table) { pic_destroy(ctx); return PIC_ENOMEM; }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { pic_destroy(ctx); return PIC_ECUDA; }
     *out = ctx;
     return PIC_OK;
@@ -655,10 +691,10 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
     const Geom &g = r.g;
     const long long ncell = (long long)g.nx * g.ny * g.nz;
     for (int s = 0; s < r.d.nspecies; ++s) {
+        if (!out->particles[s]) continue;   // fields only for this species
         if (out->count[s] < r.sp[s].n)
             return fail(ctx, PIC_EINVAL, "species %d: buffer holds %lld particles, %lld needed", s,
                         (long long)out->count[s], (long long)r.sp[s].n);
-        if (r.sp[s].n > 0 && !out->particles[s]) return fail(ctx, PIC_EINVAL, "species %d: null particle buffer", s);
     }
     cudaStream_t sm = ctx->stream;
     double *stg = (double *)ctx->staging;
@@ -674,7 +710,7 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
         const int64_t n = S.n;
         out->count[s] = n;
         double *P = out->particles[s];
-        if (n == 0) continue;
+        if (n == 0 || !P) continue;
         if (ctx->precision == PIC_FP64) {
             for (int a = 0; a < 3; ++a) {
                 if (a < g.ndim) CK(cudaMemcpyAsync(P + a * n, S.s64.x[a], sizeof(double) * n, cudaMemcpyDeviceToHost, sm));
@@ -694,6 +730,36 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
     }
     out->step = r.step;
     CK(cudaStreamSynchronize(sm));
+    return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_ctx *ctx, int run, int species, const int64_t *ids, int64_t nids, double *out) {
+    pic_status st = check_run(ctx, run);
+    if (st) return st;
+    Run &r = ctx->runs[run];
+    if (species < 0 || species >= r.d.nspecies) return fail(ctx, PIC_EINVAL, "species %d out of range", species);
+    if (nids < 0 || (nids > 0 && (!ids || !out))) return fail(ctx, PIC_EINVAL, "null ids or output");
+    SpeciesState &S = r.sp[species];
+    for (int64_t q = 0; q < nids; ++q)
+        if (ids[q] < 0 || ids[q] >= S.n) return fail(ctx, PIC_EINVAL, "id %lld out of range", (long long)ids[q]);
+    cudaStream_t sm = ctx->stream;
+    // staging holds 6 doubles per particle for `chunk` particles; the ids of a
+    // chunk are copied behind them
+    const int64_t chunk = (int64_t)(ctx->staging_bytes / (7 * sizeof(double)));
+    double *stg = (double *)ctx->staging;
+    if (ctx->precision == PIC_MIXED && S.n > 0)
+        k_id_index<<<nblk(S.n), 256, 0, sm>>>(S.mb[S.cur].id, S.n, r.perm);
+    for (int64_t a0 = 0; a0 < nids; a0 += chunk) {
+        const int64_t m = std::min(chunk, nids - a0);
+        long long *dids = reinterpret_cast<long long *>(stg + 6 * m);
+        CK(cudaMemcpyAsync(dids, ids + a0, sizeof(long long) * m, cudaMemcpyHostToDevice, sm));
+        if (ctx->precision == PIC_MIXED) k_pick_mixed<<<nblk(m), 256, 0, sm>>>(r.g, S.mb[S.cur], r.perm, dids, m, stg);
+        else k_pick64<<<nblk(m), 256, 0, sm>>>(S.s64, dids, m, r.d.ndim, stg);
+        CK(cudaGetLastError());
+        for (int a = 0; a < 6; ++a)
+            CK(cudaMemcpyAsync(out + a * nids + a0, stg + a * m, sizeof(double) * m, cudaMemcpyDeviceToHost, sm));
+        CK(cudaStreamSynchronize(sm));
+    }
     return PIC_OK;
 }
 
@@ -845,11 +911,88 @@ pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *to
 pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double ppc, double theta, const double beta[3],
                                     int profile, const double *profile_params, int method, int colocate_with,
                                     uint64_t seed) {
-    (void)species; (void)ppc; (void)theta; (void)beta; (void)profile; (void)profile_params; (void)method;
-    (void)colocate_with; (void)seed;
     pic_status st = check_run(ctx, run);
     if (st) return st;
-    return fail(ctx, PIC_ESTATE, "the Maxwell-Juttner loader is not built in this library version");
+    Run &r = ctx->runs[run];
+    const Geom &g = r.g;
+    if (species < 0 || species >= r.d.nspecies) return fail(ctx, PIC_EINVAL, "species %d out of range", species);
+    if (!(ppc > 0) || !std::isfinite(ppc)) return fail(ctx, PIC_EINVAL, "ppc must be positive");
+    if (!(theta > 0) || !std::isfinite(theta)) return fail(ctx, PIC_EINVAL, "theta must be positive");
+    if (!beta) return fail(ctx, PIC_EINVAL, "null beta");
+    const double b2 = beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2];
+    if (!(b2 < 1.0) || !std::isfinite(b2)) return fail(ctx, PIC_EINVAL, "|beta| must be below 1");
+    if (method != PIC_MJ_EXACT && method != PIC_MJ_NAIVE_BOOST && method != PIC_MJ_MLP)
+        return fail(ctx, PIC_EINVAL, "unknown loader method %d", method);
+    double L = 1.0, x0 = 0.0;
+    long long n;
+    if (profile == PIC_PROFILE_UNIFORM) {
+        n = std::llround(ppc * (double)g.nx * g.ny * g.nz);
+    } else if (profile == PIC_PROFILE_HARRIS) {
+        if (!profile_params) return fail(ctx, PIC_EINVAL, "Harris profile needs L and x0");
+        L = profile_params[0];
+        x0 = profile_params[1];
+        if (!(L > 0) || !(x0 >= 0 && x0 <= g.nx)) return fail(ctx, PIC_EINVAL, "Harris L must be > 0, 0 <= x0 <= nx");
+        n = std::llround(ppc * (double)g.ny * g.nz * L * (std::tanh((g.nx - x0) / L) - std::tanh(-x0 / L)));
+    } else {
+        return fail(ctx, PIC_EINVAL, "unknown density profile %d", profile);
+    }
+    SpeciesState &S = r.sp[species];
+    if (n > S.cap) return fail(ctx, PIC_EINVAL, "species %d: %lld particles exceed capacity %lld", species, n,
+                               (long long)S.cap);
+    int colocate = 0;
+    SpeciesState *C = nullptr;
+    if (colocate_with >= 0) {
+        if (colocate_with >= r.d.nspecies || colocate_with == species)
+            return fail(ctx, PIC_EINVAL, "colocate_with %d is not another species", colocate_with);
+        C = &r.sp[colocate_with];
+        if (C->n != n) return fail(ctx, PIC_EINVAL, "colocated species holds %lld particles, %lld needed",
+                                   (long long)C->n, n);
+        colocate = 1;
+    }
+    if (method == PIC_MJ_MLP) return mlp_load(ctx, run, species, n, theta, beta, profile, L, x0, colocate_with, seed);
+    const int naive = method == PIC_MJ_NAIVE_BOOST;
+    const double b0 = std::sqrt(b2);
+    std::vector<double> F;
+    double s0, h, psi, Z;
+    build_marginal_table(theta, naive ? 0.0 : b0, kMjTable, F, s0, h, psi, Z);
+    cudaStream_t sm = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->mj_table, F.data(), sizeof(double) * (kMjTable + 1), cudaMemcpyHostToDevice, sm));
+    const bool mixed = ctx->precision == PIC_MIXED;
+    if (mixed && C && C->cur != S.cur) {
+        // keep both species in the same buffer slot so that positions can be read from the partner
+        S.cur = C->cur;
+    }
+    Species64 d64 = S.s64, c64 = C ? C->s64 : S.s64;
+    SpeciesMixed dmx = S.mb[S.cur], cmx = C ? C->mb[C->cur] : S.mb[S.cur];
+    launch_load_mj(g, r.d.ndim, n, species, seed, profile, L, x0, theta, beta, naive, ctx->mj_table, s0, h,
+                   kMjTable, psi, Z, colocate, d64, c64, dmx, cmx, mixed ? 1 : 0, ctx->d_err, sm);
+    CK(cudaGetLastError());
+    S.n = n;
+    S.tiled = false;
+    r.sorted = false;
+    r.since_sort = 0;
+    // initial staggering of the momenta: one Boris step of -dt/2 (App. A.3.1)
+    if (mixed) {
+        FieldPtrs<float> f = fields_of<float>(r);
+        launch_node_fields(g, f, r.nfA, r.nfB, sm);
+        launch_half_back_mixed(g, r.nfA, r.nfB, S.mb[S.cur], n, (float)S.h, (float)r.d.dt, sm);
+    } else {
+        double *J[3] = {jplane<double>(r, r.jcur, 0), jplane<double>(r, r.jcur, 1), jplane<double>(r, r.jcur, 2)};
+        launch_push_fp64(g, fields_of<double>(r), J, S.s64, n, S.h, S.alpha, r.d.dt, 1, S.m_over_me, nullptr,
+                         ctx->d_err, sm);
+    }
+    CK(cudaGetLastError());
+    r.step = 0;
+    r.hist_n = 0;
+    CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, sm));
+    return read_err(ctx);
 }
 
 }  // extern "C"
+
+pic_status mlp_load(pic_ctx *ctx, int run, int species, long long n, double theta, const double beta[3], int profile,
+                    double L, double x0, int colocate_with, uint64_t seed) {
+    (void)run; (void)species; (void)n; (void)theta; (void)beta; (void)profile; (void)L; (void)x0;
+    (void)colocate_with; (void)seed;
+    return fail(ctx, PIC_ESTATE, "no trained sampler network in this context");
+}

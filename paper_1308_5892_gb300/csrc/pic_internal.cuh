@@ -19,6 +19,8 @@
 //    (SoA), FP32 momenta (SoA) and an int32 id, kept sorted by tile.
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace pic {
@@ -142,6 +144,15 @@ struct SortArgs {
 };
 void launch_sort(const SortArgs &a, cudaStream_t s);
 size_t sort_scan_scratch(long long nkeys);
+
+// mj.cu
+void build_marginal_table(double theta, double beta0, int n, std::vector<double> &F, double &s0, double &h,
+                          double &psi, double &Z);
+void launch_load_mj(const Geom &g, int ndim, long long n, int species, unsigned long long seed, int profile, double L,
+                    double x0, double theta, const double beta[3], int naive, const double *Fdev, double s0,
+                    double h, int ntab, double psi, double Z, int colocate, Species64 d64, Species64 c64,
+                    SpeciesMixed dmx, SpeciesMixed cmx, int mixed, int *err, cudaStream_t s);
+constexpr int kMjTable = 4096;
 
 // diag.cu
 template <typename R>
