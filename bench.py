@@ -50,27 +50,26 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _host_state(w, seed, chunk=1 << 24):
-    """Seeded synthetic state: co-located pairs (rho = 0), uniform positions,
-    momenta drawn per component from a normal of variance theta (a stand-in
-    for the thermal spread; the exact Maxwell-Juttner loader lives in the
-    library), zero fields."""
-    rng = np.random.default_rng(seed)
-    nz = 1 if w["ndim"] == 2 else w["nz"]
-    ncell = w["nx"] * w["ny"] * nz
-    n = int(w["ppc"] * ncell)
-    pos = np.zeros((3, n))
-    for a, L in enumerate((w["nx"], w["ny"], nz)[: w["ndim"]]):
-        pos[a] = rng.uniform(0.0, L, n)
-        np.minimum(pos[a], np.nextafter(L, 0.0), out=pos[a])
-    parts = []
-    for s in range(2):
-        p = np.empty((6, n))
-        p[:3] = pos
-        p[3:] = rng.normal(0.0, np.sqrt(w["theta"]), (3, n))
-        parts.append(p)
-    fields = np.zeros((6, nz, w["ny"], w["nx"]))
-    return fields, parts, n
+def _load(ctx, w, seed):
+    """Seeded synthetic state through the library's own Maxwell-Juttner loader:
+    co-located electron-positron pairs (rho = 0), uniform positions, rest-frame
+    Maxwell-Juttner momenta of temperature theta, zero fields."""
+    ctx.load_maxwell_juttner(0, 0, w["ppc"], w["theta"], (0.0, 0.0, 0.0), seed=seed)
+    ctx.load_maxwell_juttner(0, 1, w["ppc"], w["theta"], (0.0, 0.0, 0.0), colocate_with=0, seed=seed + 1)
+
+
+def _oracle_state(w, seed, nx, ny, nz):
+    """The same kind of state built by the oracle's own loader (for the CPU leg)."""
+    import oracle
+    from oracle import mj
+    ncell = nx * ny * (nz if w["ndim"] == 3 else 1)
+    n = int(round(w["ppc"] * ncell))
+    st = oracle.State.empty(w["ndim"], nx, ny, nz, w["dt"], w["n_x"], w["rho_sp0"])
+    pos, u0 = mj.load(seed, 0, n, w["theta"], (0.0, 0.0, 0.0), w["ndim"], nx, ny, nz)
+    _, u1 = mj.load(seed + 1, 1, n, w["theta"], (0.0, 0.0, 0.0), w["ndim"], nx, ny, nz)
+    st.species.append(oracle.Species(np.ascontiguousarray(pos), np.ascontiguousarray(u0), -1.0, 1.0))
+    st.species.append(oracle.Species(np.ascontiguousarray(pos.copy()), np.ascontiguousarray(u1), 1.0, 1.0))
+    return st, 2 * n
 
 
 class ClockSampler:
@@ -127,22 +126,18 @@ class ClockSampler:
 
 def _time_oracle_sample(w, steps, seed):
     """FP64 oracle on a 32^3 (3D) or 64^2 (2D) box with the workload's ppc and
-    temperature; returns (particle-steps/ns, seconds, particles, steps)."""
+    temperature; returns (particle-steps/ns, seconds, particles, steps, sizes)."""
     import oracle
     sw = dict(w)
     if w["ndim"] == 3:
         sw.update(nx=32, ny=32, nz=32)
     else:
-        sw.update(nx=min(w["nx"], 64), ny=min(w["ny"], 64))
-    fields, parts, n = _host_state(sw, seed)
-    st = oracle.State.empty(w["ndim"], sw["nx"], sw["ny"], sw["nz"], w["dt"], w["n_x"], w["rho_sp0"])
-    for s, q in enumerate((-1.0, 1.0)):
-        st.species.append(oracle.Species(np.ascontiguousarray(parts[s][:3]), np.ascontiguousarray(parts[s][3:]), q, 1.0))
+        sw.update(nx=min(w["nx"], 64), ny=min(w["ny"], 64), nz=1)
+    st, npart = _oracle_state(w, seed, sw["nx"], sw["ny"], sw["nz"])
     t0 = time.perf_counter()
     oracle.step(st, steps)
     dt = time.perf_counter() - t0
-    ps = 2 * n * steps
-    return ps / (dt * 1e9), dt, 2 * n, steps, sw
+    return npart * steps / (dt * 1e9), dt, npart, steps, sw
 
 
 def run_reference(args, w):
@@ -188,10 +183,11 @@ def run_ours(args, w):
             dist.barrier()
         torch.cuda.synchronize()
 
-    fields, parts, n = _host_state(w, seed=2 + rank)
     nz = 1 if w["ndim"] == 2 else w["nz"]
+    n = int(round(w["ppc"] * w["nx"] * w["ny"] * nz))
     desc = pic.run_desc(w["ndim"], w["nx"], w["ny"], nz, w["n_x"], w["rho_sp0"], w["dt"],
                         [(-1.0, 1.0, n), (1.0, 1.0, n)])
+    seed = 2 + 1000 * rank
     npart = 2 * n
     results = {}
     legs = ((pic.PIC_MIXED, "mixed"),) if args.no_fp64 else ((pic.PIC_MIXED, "mixed"), (pic.PIC_FP64, "fp64"))
@@ -199,7 +195,7 @@ def run_ours(args, w):
         steps = args.steps if prec == pic.PIC_MIXED else max(1, min(args.steps, args.fp64_steps))
         ctx = pic.Context([desc], precision=prec, flags=pic.PIC_FLAG_TIMING, tile=tuple(args.tile),
                           sort_interval=args.sort_interval)
-        ctx.set_state(0, fields, parts)
+        _load(ctx, w, seed)
         ctx.step(args.warmup)
         ctx.kernel_time(pic.PIC_KERNEL_PUSH, reset=True)
         stream = torch.cuda.current_stream()
@@ -234,22 +230,26 @@ def run_ours(args, w):
     # end-to-end through the C ABI with host buffers: upload the state, run the
     # timed steps, read the state back; all copies inside the timed region
     e2e_s = None
-    h2d = fields.nbytes + sum(p.nbytes for p in parts)
-    d2h = h2d
+    h2d = d2h = 0
     if not args.no_e2e:
-        e2e_s = _e2e(pic, torch, desc, fields, parts, args, barrier)
+        e2e_s, h2d, d2h = _e2e(pic, torch, desc, w, seed, args, barrier)
     if args.no_fp64:
         results["fp64"] = None
     return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist)
 
 
-def _e2e(pic, torch, desc, fields, parts, args, barrier):
+def _e2e(pic, torch, desc, w, seed, args, barrier):
+    """End to end through the C ABI with host buffers: the timed region uploads
+    the whole state from pinned host memory, runs the steps and reads the whole
+    state back into pinned host memory."""
+    ctx = pic.Context([desc], precision=pic.PIC_MIXED)
+    _load(ctx, w, seed)
+    fields, parts, _ = ctx.get_state(0)
     pin_f = torch.from_numpy(fields).pin_memory().numpy()
     pin_p = [torch.from_numpy(p).pin_memory().numpy() for p in parts]
     out_f = torch.empty(fields.shape, dtype=torch.float64).pin_memory().numpy()
     out_p = [torch.empty(p.shape, dtype=torch.float64).pin_memory().numpy() for p in parts]
-    ctx = pic.Context([desc], precision=pic.PIC_MIXED)
-    ctx.set_state(0, pin_f, pin_p)
+    del fields, parts
     ctx.step(args.warmup)
     barrier()
     t0 = time.perf_counter()
@@ -259,7 +259,8 @@ def _e2e(pic, torch, desc, fields, parts, args, barrier):
     barrier()
     e2e_s = time.perf_counter() - t0
     ctx.close()
-    return e2e_s
+    nbytes = pin_f.nbytes + sum(p.nbytes for p in pin_p)
+    return e2e_s, nbytes, nbytes
 
 
 def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist):

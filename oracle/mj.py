@@ -7,7 +7,7 @@ vector n, temperature theta = T/(m c^2), mu = 1/theta, Gamma0 = (1-beta0^2)^-1/2
      inverse of its cumulative distribution, y = J^-1(w);
   2. u given y from the conditional of Eq. distr_u, solved as
      l(a_y u) = w' l(a_y), l(x) = (1 + x) exp(-x), a_y = mu Gamma0 sqrt(1+y^2)
-     (Eq. finding_u; here with the closed-form root 1 + x = -W_{-1}(-w' l(a)/e));
+     (Eq. finding_u), written for t = a_y (u - 1) and solved by bisection;
   3. r = sqrt(u^2 - 1), phi uniform, the perpendicular momenta gamma_y r (cos phi, sin phi),
      which undoes the change of variables of App. D.
 Readings (listed in the design notes): w is a continuous uniform, not a random
@@ -152,12 +152,33 @@ class MarginalInverse:
 
 # ------------------------------------------------------------------ conditional and assembly
 
+def conditional_t(a, w, iters=200):
+    """t = a (u - 1) >= 0 with l(a + t) = w l(a) (Eq. finding_u), i.e.
+    log1p(t / (1 + a)) - t = log w, solved by bisection (robust for any a)."""
+    a = np.asarray(a, dtype=np.float64)
+    lw = np.log(w)
+    lo = np.zeros_like(a)
+    hi = -lw * (1.0 + a) / a * 1.01 + 1e-300
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        f = np.log1p(mid / (1.0 + a)) - mid - lw
+        pos = f > 0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+    return 0.5 * (lo + hi)
+
+
 def conditional_u(y, w, theta, beta0):
-    """u >= 1 with l(a u) = w l(a), a = mu Gamma0 sqrt(1+y^2) (Eq. finding_u):
-    1 + a u = -W_{-1}(-w l(a) / e)."""
+    """u >= 1 of Eq. finding_u given y (a = mu Gamma0 sqrt(1 + y^2))."""
     mu, G0 = _params(theta, beta0)
     a = mu * G0 * np.sqrt(1.0 + y * y)
-    # w l(a)/e = w (1 + a) exp(-a - 1), in log form to stay finite for large a
+    return 1.0 + conditional_t(a, w) / a
+
+
+def conditional_u_lambertw(y, w, theta, beta0):
+    """The same root in closed form, 1 + a u = -W_{-1}(-w l(a)/e), for moderate a."""
+    mu, G0 = _params(theta, beta0)
+    a = mu * G0 * np.sqrt(1.0 + y * y)
     logz = np.log(w) + np.log1p(a) - a - 1.0
     x1 = -np.real(special.lambertw(-np.exp(logz), k=-1))
     return (x1 - 1.0) / a
@@ -181,8 +202,10 @@ def sample_momenta(w_py, w_u, w_phi, theta, beta):
     b0 = float(np.linalg.norm(beta))
     n, e1, e2 = basis(beta)
     y = MarginalInverse(theta, b0)(w_py)
-    u = conditional_u(y, w_u, theta, b0)
-    r = np.sqrt(np.maximum(u * u - 1.0, 0.0))
+    mu, G0 = _params(theta, b0)
+    a = mu * G0 * np.sqrt(1.0 + y * y)
+    um1 = conditional_t(a, w_u) / a          # u - 1, accurate also when u is close to 1
+    r = np.sqrt(um1 * (um1 + 2.0))
     gy = np.sqrt(1.0 + y * y)
     phi = 2.0 * np.pi * w_phi
     p1, p2 = gy * r * np.cos(phi), gy * r * np.sin(phi)

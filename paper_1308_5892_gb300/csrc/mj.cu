@@ -11,7 +11,7 @@
 //             built on the host in FP64) and Newton steps on the exact
 //             density, J being re-integrated from the nearest table node;
 //   u         from Eq. finding_u, l(a u) = w' l(a), l(x) = (1+x) e^-x,
-//             a = mu Gamma0 sqrt(1+y^2), by Newton on log l;
+//             a = mu Gamma0 sqrt(1+y^2), by Newton on t = a (u - 1);
 //   p_perp    gamma_y sqrt(u^2-1) (cos phi, sin phi), phi uniform (undoing the
 //             change of variables of App. D), in the plane orthogonal to n.
 // All arithmetic of the momenta is FP64; the mixed path stores the result as
@@ -121,20 +121,23 @@ __device__ double inverse_marginal(const Table &t, double w) {
     return sinh(sig + t.m.psi);
 }
 
-// u >= 1 from log l(a u) = log w + log l(a), log l(x) = log(1+x) - x, by Newton.
-__device__ double conditional_u(double a, double w) {
-    const double target = log(w) + log1p(a) - a;
-    double x = a - log(w);
-    for (int it = 0; it < 40; ++it) {
-        const double f = log1p(x) - x - target;
-        const double fp = -x / (1.0 + x);
-        double nx = x - f / fp;
-        if (nx < a) nx = a;
-        const bool done = fabs(nx - x) <= 1e-15 * nx;
-        x = nx;
+// t = a (u - 1) >= 0 from l(a + t) = w l(a) (Eq. finding_u), written as
+// log1p(t / (1 + a)) - t = log w and solved by Newton from t = -log w (the
+// large-a limit); the function is concave and decreasing in t, so the steps
+// converge monotonically once on the right of the root.
+__device__ double conditional_t(double a, double w) {
+    const double lw = log(w);
+    double t = -lw;
+    for (int it = 0; it < 60; ++it) {
+        const double f = log1p(t / (1.0 + a)) - t - lw;
+        const double fp = 1.0 / (1.0 + a + t) - 1.0;
+        double nt = t - f / fp;
+        if (nt < 0.0) nt = 0.5 * t;
+        const bool done = fabs(nt - t) <= 1e-16 * (nt + 1e-300);
+        t = nt;
         if (done) break;
     }
-    return x / a;
+    return t;
 }
 
 struct LoadArgs {
@@ -172,9 +175,8 @@ __global__ void k_load_mj(LoadArgs a) {
         const double G0 = 1.0 / sqrt(1.0 - a.sb0 * a.sb0);
         const double gy = sqrt(1.0 + y * y);
         const double aa = mu * G0 * gy;
-        const double u = conditional_u(aa, w[4]);
-        const double um1 = u - 1.0;
-        const double r = sqrt(fmax(um1 * (u + 1.0), 0.0));
+        const double um1 = conditional_t(aa, w[4]) / aa;   // u - 1
+        const double r = sqrt(um1 * (um1 + 2.0));
         double sphi, cphi;
         sincospi(2.0 * w[5], &sphi, &cphi);
         double par = y, q1 = gy * r * cphi, q2 = gy * r * sphi;

@@ -90,6 +90,13 @@ def test_conditional_is_exact():
     assert np.allclose(back, w[4], rtol=1e-10, atol=1e-14)
     assert np.all(u >= 1.0)
     assert _ks(back) < 1.63 / np.sqrt(n)
+    # closed form with the lower Lambert-W branch where it is finite
+    assert np.allclose(mj.conditional_u_lambertw(y, w[4], theta, b), u, rtol=1e-12)
+    # large a (cold, fast drift): still finite and exact
+    uu = mj.conditional_u(np.array([0.0, 5.0]), np.array([0.3, 1e-9]), 0.01, np.sqrt(8 / 9.0))
+    aa = 100 * 3 * np.sqrt(1 + np.array([0.0, 25.0]))
+    assert np.all(np.isfinite(uu))
+    assert np.allclose(np.exp(l(aa * uu) - l(aa)), [0.3, 1e-9], rtol=1e-9)
 
 
 @pytest.mark.parametrize("theta,beta0", [(0.1, 0.0), (1.0, 0.5), (0.3, 0.9), (5.0, 0.3)])
