@@ -247,6 +247,41 @@ pic_status pic_get_counters(const pic_ctx *ctx, int64_t *launches_per_step, doub
  * pic_kernel_time with reset != 0.  Synchronises. */
 pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *total_ms, int64_t *launches);
 
+/* Gauss-law check for callers that must not allocate device memory.
+ *
+ * The paper has no counterpart of this entry point: it is a library service.
+ * It computes, for a caller-owned FP64 state on the current device, the same
+ * two numbers as pic_diagnostics: out[0] = max over nodes of |div e - rho~|
+ * and out[1] = max over species and nodes of |rho~_s|, rho~_s = alpha_s times
+ * the CIC weights of the positions.  It exists for callers that cannot call
+ * cudaMalloc (or any allocating routine) where they need the check: a step
+ * loop whose memory pool is fixed up front, a host framework that owns the
+ * device allocator, or code that must not enter the allocator and its
+ * implicit synchronisation.  No context is needed and nothing is allocated:
+ * the only scratch is a static device array of 2^20 doubles inside the
+ * library, which every GPU that loads the library keeps for the life of the
+ * process.
+ *  ndim, nx,ny,nz  grid (nz = 1 when ndim = 2); nx*ny*nz at most 1048576,
+ *                  larger grids return PIC_EINVAL with a message on stderr
+ *  e               device pointer, 3 planes of nz*ny*nx doubles (e_x, e_y,
+ *                  e_z), plain layout indexed (k*ny + j)*nx + i, periodic
+ *  nspecies        0..PIC_MAX_SPECIES
+ *  counts, alpha   host arrays: particles and alpha_s per species
+ *  pos             host array of device pointers, each 3*counts[s] doubles
+ *                  (planes x, y, z; z ignored in 2D), positions in [0, n)
+ *  out             device pointer to 2 doubles, written by the call
+ *  stream          cudaStream_t the work is queued on (NULL: default stream)
+ * The call is asynchronous on `stream`.  The first call on a device looks up
+ * the scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the one scratch array and clears it before use: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  Returns PIC_EINVAL for invalid arguments and
+ * PIC_ECUDA when a CUDA call fails. */
+pic_status pic_gauss_residual_static(int ndim, int nx, int ny, int nz, const double *e, int nspecies,
+                                     const int64_t *counts, const double *const *pos, const double *alpha,
+                                     double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
