@@ -247,6 +247,35 @@ pic_status pic_get_counters(const pic_ctx *ctx, int64_t *launches_per_step, doub
  * pic_kernel_time with reset != 0.  Synchronises. */
 pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *total_ms, int64_t *launches);
 
+/* ---- learned sampler of the loader (method PIC_MJ_MLP) ----
+ * A small network p_par = f(theta, beta0, w) replaces the inversion of the
+ * cumulative marginal of Eq. distr_y: 3 -> 64 -> 64 -> 64 -> 1, tanh hidden
+ * layers, inputs (log10 theta + 0.5)/1.5, 2 beta0/0.95 - 1, probit(w)/3,
+ * output o with asinh(p_par) = atanh(beta0) + asinh(sqrt(theta)) o; valid for
+ * 0.01 <= theta <= 10 and 0 <= beta0 <= 0.95.  PIC_MLP_PARAMS FP32 parameters
+ * in the order W1[64][3] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4. */
+#define PIC_MLP_PARAMS 8641
+
+/* Train the context's network on the GPU: each of `steps` Adam steps (cosine
+ * decay from lr) draws `batch` fresh samples (32..8192) from the exact
+ * sampler on a 16 x 12 grid of (theta, beta0) and minimises the mean squared
+ * error of o.  Starts from Xavier-uniform weights of `seed` unless weights
+ * were set.  *final_loss receives the mean loss of the last steps. */
+pic_status pic_mlp_train(pic_ctx *ctx, int steps, int batch, double lr, uint64_t seed, double *final_loss);
+pic_status pic_mlp_set_weights(pic_ctx *ctx, const float *w);
+pic_status pic_mlp_get_weights(pic_ctx *ctx, float *w);
+/* One forward and backward pass of the FP32 training kernel on a host batch:
+ * x holds 3 planes of n inputs, target n outputs (1 <= n <= 8192); grad
+ * receives d(loss)/d(parameters) of loss = mean (o - target)^2. */
+pic_status pic_mlp_gradients(pic_ctx *ctx, const float *x, const float *target, int n, float *grad, double *loss);
+/* FP16 inference (FP32 accumulation) of n host inputs (3 planes) into out. */
+pic_status pic_mlp_infer(pic_ctx *ctx, const float *x, int64_t n, float *out);
+/* Drift component p_par of given uniforms w (host, n values) for one
+ * (theta, beta0), by method PIC_MJ_EXACT or PIC_MJ_MLP, into y (host);
+ * *device_ms receives the kernel time. */
+pic_status pic_mj_sample_marginal(pic_ctx *ctx, double theta, double beta0, const double *w, int64_t n, double *y,
+                                  int method, double *device_ms);
+
 /* Gauss-law check for callers that must not allocate device memory.
  *
  * The paper has no counterpart of this entry point: it is a library service.

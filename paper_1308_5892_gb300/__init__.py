@@ -28,7 +28,10 @@ ABI_FUNCTIONS = [
     "pic_abi_version", "pic_init", "pic_destroy", "pic_last_error", "pic_set_state", "pic_get_state",
     "pic_set_uniform_field", "pic_load_maxwell_juttner", "pic_step", "pic_sync", "pic_diagnostics",
     "pic_energy_history", "pic_get_tuning", "pic_get_counters", "pic_kernel_time", "pic_get_particles",
+    "pic_mlp_train", "pic_mlp_set_weights", "pic_mlp_get_weights", "pic_mlp_gradients", "pic_mlp_infer",
+    "pic_mj_sample_marginal", "pic_gauss_residual_static",
 ]
+MLP_PARAMS = 8641
 
 
 class PicError(RuntimeError):
@@ -115,6 +118,15 @@ def lib(build_if_missing=True):
                              ctypes.POINTER(ctypes.c_int64)], st),
         "pic_get_particles": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_double)], st),
+        "pic_mlp_train": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                           ctypes.POINTER(ctypes.c_double)], st),
+        "pic_mlp_set_weights": ([P, ctypes.POINTER(ctypes.c_float)], st),
+        "pic_mlp_get_weights": ([P, ctypes.POINTER(ctypes.c_float)], st),
+        "pic_mlp_gradients": ([P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)], st),
+        "pic_mlp_infer": ([P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.POINTER(ctypes.c_float)], st),
+        "pic_mj_sample_marginal": ([P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)], st),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -318,3 +330,44 @@ class Context:
         self._check(self._L.pic_get_particles(self.h, run, species, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                               len(ids), _dptr(out)))
         return out
+
+    # ---- learned sampler of the loader
+    def mlp_train(self, steps=4000, batch=4096, lr=3e-3, seed=1):
+        loss = ctypes.c_double()
+        self._check(self._L.pic_mlp_train(self.h, steps, batch, lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == MLP_PARAMS
+        self._check(self._L.pic_mlp_set_weights(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def mlp_get_weights(self):
+        w = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(self._L.pic_mlp_get_weights(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return w
+
+    def mlp_gradients(self, x, target):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        f = ctypes.POINTER(ctypes.c_float)
+        self._check(self._L.pic_mlp_gradients(self.h, x.ctypes.data_as(f), t.ctypes.data_as(f), t.size,
+                                               g.ctypes.data_as(f), ctypes.byref(loss)))
+        return g, loss.value
+
+    def mlp_infer(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.zeros(x.shape[1], dtype=np.float32)
+        f = ctypes.POINTER(ctypes.c_float)
+        self._check(self._L.pic_mlp_infer(self.h, x.ctypes.data_as(f), x.shape[1], out.ctypes.data_as(f)))
+        return out
+
+    def mj_sample_marginal(self, theta, beta0, w, method=PIC_MJ_EXACT):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        y = np.zeros_like(w)
+        ms = ctypes.c_double()
+        self._check(self._L.pic_mj_sample_marginal(self.h, theta, beta0, _dptr(w), w.size, _dptr(y), method,
+                                                    ctypes.byref(ms)))
+        return y, ms.value

@@ -70,6 +70,12 @@ struct pic_ctx {
     void *staging = nullptr;
     size_t staging_bytes = 0;
     double *mj_table = nullptr;     // cumulative marginal of the loader, kMjTable + 1 values
+    // learned sampler of the loader (mlp.cu)
+    float *mlpW = nullptr, *mlpG = nullptr, *mlpM = nullptr, *mlpV = nullptr, *mlpX = nullptr, *mlpT = nullptr;
+    void *mlpWh = nullptr;
+    double *mlpLoss = nullptr, *mlpF = nullptr, *mlpPar = nullptr;
+    bool mlp_tables = false, mlp_ready = false, mlp_init = false;
+    int mlp_step = 0;
     std::vector<std::pair<void *, size_t>> allocs;
     std::string err;
     int64_t launches_per_step = 0;
@@ -586,7 +592,26 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
     ctx->staging_bytes = stage;
     ctx->staging = dev_alloc(ctx, stage);
     ctx->mj_table = (double *)dev_alloc(ctx, sizeof(double) * (kMjTable + 1));
-    if (!ctx->staging || !ctx->mj_table) { pic_destroy(ctx); return PIC_ENOMEM; }
+    const int ncombo = kMlpTheta * kMlpBeta;
+    ctx->mlpW = (float *)dev_alloc(ctx, sizeof(float) * kMlpParams);
+    ctx->mlpG = (float *)dev_alloc(ctx, sizeof(float) * kMlpParams);
+    ctx->mlpM = (float *)dev_alloc(ctx, sizeof(float) * kMlpParams);
+    ctx->mlpV = (float *)dev_alloc(ctx, sizeof(float) * kMlpParams);
+    ctx->mlpWh = dev_alloc(ctx, 2 * kMlpParams);
+    ctx->mlpX = (float *)dev_alloc(ctx, sizeof(float) * 3 * kMlpBatchMax);
+    ctx->mlpT = (float *)dev_alloc(ctx, sizeof(float) * kMlpBatchMax);
+    ctx->mlpLoss = (double *)dev_alloc(ctx, sizeof(double));
+    ctx->mlpF = (double *)dev_alloc(ctx, sizeof(double) * (size_t)ncombo * (kMjTable + 1));
+    ctx->mlpPar = (double *)dev_alloc(ctx, sizeof(double) * 8 * ncombo);
+    if (!ctx->staging || !ctx->mj_table || !ctx->mlpW || !ctx->mlpG || !ctx->mlpM || !ctx->mlpV || !ctx->mlpWh ||
+        !ctx->mlpX || !ctx->mlpT || !ctx->mlpLoss || !ctx->mlpF || !ctx->mlpPar) {
+        pic_destroy(ctx);
+        return PIC_ENOMEM;
+    }
+    if (cudaMemsetAsync(ctx->mlpG, 0, sizeof(float) * kMlpParams, ctx->stream) != cudaSuccess) {
+        pic_destroy(ctx);
+        return PIC_ECUDA;
+    }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { pic_destroy(ctx); return PIC_ECUDA; }
     *out = ctx;
     return PIC_OK;
@@ -990,9 +1015,237 @@ pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double p
 
 }  // extern "C"
 
+// ------------------------------------------------------------ learned sampler
+
+namespace {
+
+double mlp_theta(int k) { return std::pow(10.0, -2.0 + 3.0 * k / (kMlpTheta - 1)); }
+double mlp_beta(int j) { return 0.95 * j / (kMlpBeta - 1); }
+
+pic_status mlp_build_tables(pic_ctx *ctx) {
+    if (ctx->mlp_tables) return PIC_OK;
+    const int ncombo = kMlpTheta * kMlpBeta;
+    std::vector<double> F((size_t)ncombo * (kMjTable + 1)), par(8 * (size_t)ncombo);
+    for (int k = 0; k < kMlpTheta; ++k)
+        for (int j = 0; j < kMlpBeta; ++j) {
+            const int c = k * kMlpBeta + j;
+            std::vector<double> f;
+            double s0, h, psi, Z;
+            const double th = mlp_theta(k), b0 = mlp_beta(j);
+            build_marginal_table(th, b0, kMjTable, f, s0, h, psi, Z);
+            std::copy(f.begin(), f.end(), F.begin() + (size_t)c * (kMjTable + 1));
+            const double pv[8] = {1.0 / th, 1.0 / std::sqrt(1.0 - b0 * b0), psi, Z, s0, h, th, b0};
+            std::copy(pv, pv + 8, par.begin() + 8 * c);
+        }
+    CK(cudaMemcpyAsync(ctx->mlpF, F.data(), sizeof(double) * F.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->mlpPar, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_tables = true;
+    return PIC_OK;
+}
+
+// Xavier-uniform initial weights, zero biases (splitmix64 stream of the seed).
+void mlp_init_weights(std::vector<float> &w, uint64_t seed) {
+    auto next = [&seed]() {
+        uint64_t z = (seed += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1p-53;
+    };
+    w.assign(kMlpParams, 0.f);
+    const int H = 64;
+    auto fill = [&](int off, int fan_in, int fan_out) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int q = 0; q < fan_in * fan_out; ++q) w[off + q] = (float)((2.0 * next() - 1.0) * a);
+    };
+    fill(0, 3, H);
+    fill(H * 3 + H, H, H);
+    fill(H * 3 + H + H * H + H, H, H);
+    fill(H * 3 + H + 2 * (H * H + H), H, 1);
+}
+
+pic_status mlp_upload(pic_ctx *ctx, const float *w) {
+    CK(cudaMemcpyAsync(ctx->mlpW, w, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlpM, 0, sizeof(float) * kMlpParams, ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlpV, 0, sizeof(float) * kMlpParams, ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlpG, 0, sizeof(float) * kMlpParams, ctx->stream));
+    launch_mlp_to_half(ctx->mlpW, ctx->mlpWh, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->mlp_step = 0;
+    ctx->mlp_init = true;
+    return PIC_OK;
+}
+
+}  // namespace
+
 pic_status mlp_load(pic_ctx *ctx, int run, int species, long long n, double theta, const double beta[3], int profile,
                     double L, double x0, int colocate_with, uint64_t seed) {
-    (void)run; (void)species; (void)n; (void)theta; (void)beta; (void)profile; (void)L; (void)x0;
-    (void)colocate_with; (void)seed;
-    return fail(ctx, PIC_ESTATE, "no trained sampler network in this context");
+    if (!ctx->mlp_ready) return fail(ctx, PIC_ESTATE, "the sampler network is not trained (pic_mlp_train or pic_mlp_set_weights)");
+    Run &r = ctx->runs[run];
+    SpeciesState &S = r.sp[species];
+    SpeciesState *C = colocate_with >= 0 ? &r.sp[colocate_with] : nullptr;
+    const bool mixed = ctx->precision == PIC_MIXED;
+    if (mixed && C && C->cur != S.cur) S.cur = C->cur;
+    cudaStream_t sm = ctx->stream;
+    launch_load_mj_mlp(r.g, r.d.ndim, n, species, seed, profile, L, x0, theta, beta, ctx->mlpWh, C ? 1 : 0, S.s64,
+                       C ? C->s64 : S.s64, S.mb[S.cur], C ? C->mb[C->cur] : S.mb[S.cur], mixed ? 1 : 0, ctx->d_err, sm);
+    CK(cudaGetLastError());
+    S.n = n;
+    S.tiled = false;
+    r.sorted = false;
+    r.since_sort = 0;
+    if (mixed) {
+        FieldPtrs<float> f = fields_of<float>(r);
+        launch_node_fields(r.g, f, r.nfA, r.nfB, sm);
+        launch_half_back_mixed(r.g, r.nfA, r.nfB, S.mb[S.cur], n, (float)S.h, (float)r.d.dt, sm);
+    } else {
+        double *J[3] = {jplane<double>(r, r.jcur, 0), jplane<double>(r, r.jcur, 1), jplane<double>(r, r.jcur, 2)};
+        launch_push_fp64(r.g, fields_of<double>(r), J, S.s64, n, S.h, S.alpha, r.d.dt, 1, S.m_over_me, nullptr,
+                         ctx->d_err, sm);
+    }
+    CK(cudaGetLastError());
+    r.step = 0;
+    r.hist_n = 0;
+    CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, sm));
+    return read_err(ctx);
 }
+
+extern "C" {
+
+pic_status pic_mlp_set_weights(pic_ctx *ctx, const float *w) {
+    if (!ctx) return PIC_EINVAL;
+    if (!w) return fail(ctx, PIC_EINVAL, "null weights");
+    for (int q = 0; q < kMlpParams; ++q)
+        if (!std::isfinite(w[q])) return fail(ctx, PIC_ENUMERIC, "non-finite weight %d", q);
+    pic_status st = mlp_upload(ctx, w);
+    if (st) return st;
+    ctx->mlp_ready = true;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
+pic_status pic_mlp_get_weights(pic_ctx *ctx, float *w) {
+    if (!ctx) return PIC_EINVAL;
+    if (!w) return fail(ctx, PIC_EINVAL, "null output");
+    if (!ctx->mlp_init) return fail(ctx, PIC_ESTATE, "no weights yet");
+    CK(cudaMemcpyAsync(w, ctx->mlpW, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
+pic_status pic_mlp_gradients(pic_ctx *ctx, const float *x, const float *target, int n, float *grad, double *loss) {
+    if (!ctx) return PIC_EINVAL;
+    if (n < 1 || n > kMlpBatchMax || !x || !target || !grad) return fail(ctx, PIC_EINVAL, "batch of 1..%d samples", kMlpBatchMax);
+    if (!ctx->mlp_init) return fail(ctx, PIC_ESTATE, "no weights yet");
+    cudaStream_t sm = ctx->stream;
+    for (int c = 0; c < 3; ++c)
+        CK(cudaMemcpyAsync(ctx->mlpX + (size_t)c * n, x + (size_t)c * n, sizeof(float) * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(ctx->mlpT, target, sizeof(float) * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemsetAsync(ctx->mlpG, 0, sizeof(float) * kMlpParams, sm));
+    CK(cudaMemsetAsync(ctx->mlpLoss, 0, sizeof(double), sm));
+    launch_mlp_fwd_bwd(ctx->mlpW, ctx->mlpX, ctx->mlpT, n, ctx->mlpG, ctx->mlpLoss, sm);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(grad, ctx->mlpG, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, sm));
+    double l = 0.0;
+    CK(cudaMemcpyAsync(&l, ctx->mlpLoss, sizeof(double), cudaMemcpyDeviceToHost, sm));
+    CK(cudaMemsetAsync(ctx->mlpG, 0, sizeof(float) * kMlpParams, sm));
+    CK(cudaStreamSynchronize(sm));
+    if (loss) *loss = l;
+    return PIC_OK;
+}
+
+pic_status pic_mlp_train(pic_ctx *ctx, int steps, int batch, double lr, uint64_t seed, double *final_loss) {
+    if (!ctx) return PIC_EINVAL;
+    if (steps < 1 || batch < 32 || batch > kMlpBatchMax || !(lr > 0))
+        return fail(ctx, PIC_EINVAL, "steps >= 1, 32 <= batch <= %d, lr > 0", kMlpBatchMax);
+    pic_status st = mlp_build_tables(ctx);
+    if (st) return st;
+    if (!ctx->mlp_init) {
+        std::vector<float> w;
+        mlp_init_weights(w, seed);
+        st = mlp_upload(ctx, w.data());
+        if (st) return st;
+    }
+    cudaStream_t sm = ctx->stream;
+    const int ncombo = kMlpTheta * kMlpBeta;
+    const int tail = std::max(1, std::min(100, steps / 10));
+    CK(cudaMemsetAsync(ctx->mlpLoss, 0, sizeof(double), sm));
+    for (int k = 0; k < steps; ++k) {
+        launch_mlp_data(ctx->mlpF, ctx->mlpPar, ncombo, seed, (long long)(ctx->mlp_step + k) * batch, batch, ctx->mlpX,
+                        ctx->mlpT, sm);
+        launch_mlp_fwd_bwd(ctx->mlpW, ctx->mlpX, ctx->mlpT, batch, ctx->mlpG, ctx->mlpLoss, sm);
+        // the reported loss sums the last `tail` steps only
+        if (k == steps - tail - 1) CK(cudaMemsetAsync(ctx->mlpLoss, 0, sizeof(double), sm));
+        // cosine decay of the learning rate
+        const double f = 0.5 * (1.0 + std::cos(M_PI * (double)k / steps));
+        launch_adam(ctx->mlpW, ctx->mlpG, ctx->mlpM, ctx->mlpV, ctx->mlp_step + k + 1, (float)(lr * (0.02 + 0.98 * f)), sm);
+    }
+    ctx->mlp_step += steps;
+    launch_mlp_to_half(ctx->mlpW, ctx->mlpWh, sm);
+    CK(cudaGetLastError());
+    double l = 0.0;
+    CK(cudaMemcpyAsync(&l, ctx->mlpLoss, sizeof(double), cudaMemcpyDeviceToHost, sm));
+    CK(cudaStreamSynchronize(sm));
+    if (final_loss) *final_loss = l / tail;
+    ctx->mlp_ready = true;
+    return PIC_OK;
+}
+
+pic_status pic_mlp_infer(pic_ctx *ctx, const float *x, int64_t n, float *out) {
+    if (!ctx) return PIC_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !out))) return fail(ctx, PIC_EINVAL, "null input or output");
+    if (!ctx->mlp_init) return fail(ctx, PIC_ESTATE, "no weights yet");
+    cudaStream_t sm = ctx->stream;
+    const int64_t chunk = kMlpBatchMax;
+    for (int64_t a0 = 0; a0 < n; a0 += chunk) {
+        const int m = (int)std::min(chunk, n - a0);
+        for (int c = 0; c < 3; ++c)
+            CK(cudaMemcpyAsync(ctx->mlpX + (size_t)c * m, x + (size_t)c * n + a0, sizeof(float) * m,
+                               cudaMemcpyHostToDevice, sm));
+        launch_mlp_infer(ctx->mlpWh, ctx->mlpX, m, ctx->mlpT, sm);
+        CK(cudaMemcpyAsync(out + a0, ctx->mlpT, sizeof(float) * m, cudaMemcpyDeviceToHost, sm));
+    }
+    CK(cudaStreamSynchronize(sm));
+    return PIC_OK;
+}
+
+pic_status pic_mj_sample_marginal(pic_ctx *ctx, double theta, double beta0, const double *w, int64_t n, double *y,
+                                  int method, double *device_ms) {
+    if (!ctx) return PIC_EINVAL;
+    if (!(theta > 0) || !(beta0 >= 0 && beta0 < 1) || n < 0 || (n > 0 && (!w || !y)))
+        return fail(ctx, PIC_EINVAL, "theta > 0, 0 <= beta0 < 1, non-null buffers");
+    if (method != PIC_MJ_EXACT && method != PIC_MJ_MLP) return fail(ctx, PIC_EINVAL, "method EXACT or MLP");
+    if (method == PIC_MJ_MLP && !ctx->mlp_ready) return fail(ctx, PIC_ESTATE, "the sampler network is not trained");
+    std::vector<double> F;
+    double s0, h, psi, Z;
+    build_marginal_table(theta, beta0, kMjTable, F, s0, h, psi, Z);
+    cudaStream_t sm = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->mj_table, F.data(), sizeof(double) * (kMjTable + 1), cudaMemcpyHostToDevice, sm));
+    const int64_t chunk = (int64_t)(ctx->staging_bytes / (2 * sizeof(double)));
+    double *stg = (double *)ctx->staging;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float total = 0.f;
+    for (int64_t a0 = 0; a0 < n; a0 += chunk) {
+        const int m = (int)std::min(chunk, n - a0);
+        CK(cudaMemcpyAsync(stg, w + a0, sizeof(double) * m, cudaMemcpyHostToDevice, sm));
+        CK(cudaEventRecord(e0, sm));
+        launch_sample_par(ctx->mj_table, s0, h, psi, Z, ctx->mlpWh, method == PIC_MJ_MLP, theta, beta0, stg, m,
+                          stg + m, sm);
+        CK(cudaEventRecord(e1, sm));
+        CK(cudaMemcpyAsync(y + a0, stg + m, sizeof(double) * m, cudaMemcpyDeviceToHost, sm));
+        CK(cudaStreamSynchronize(sm));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        total += ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    if (device_ms) *device_ms = total;
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -154,6 +154,25 @@ void launch_load_mj(const Geom &g, int ndim, long long n, int species, unsigned 
                     SpeciesMixed dmx, SpeciesMixed cmx, int mixed, int *err, cudaStream_t s);
 constexpr int kMjTable = 4096;
 
+// mlp.cu
+constexpr int kMlpParams = 64 * 3 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1;
+constexpr int kMlpTheta = 16, kMlpBeta = 12;        // training grid of (theta, beta0)
+constexpr int kMlpBatchMax = 8192;
+size_t mlp_train_smem();
+void launch_mlp_fwd_bwd(const float *W, const float *X, const float *T, int n, float *grad, double *loss,
+                        cudaStream_t s);
+void launch_adam(float *W, float *g, float *m, float *v, int step, float lr, cudaStream_t s);
+void launch_mlp_to_half(const float *W, void *Wh, cudaStream_t s);
+void launch_mlp_infer(const void *Wh, const float *X, int n, float *out, cudaStream_t s);
+void launch_mlp_data(const double *F, const double *par, int ncombo, unsigned long long seed, long long base, int n,
+                     float *X, float *T, cudaStream_t s);
+void launch_sample_par(const double *F, double s0, double h, double psi, double Z, const void *Wh, int use_mlp,
+                       double theta, double beta0, const double *w, int n, double *y, cudaStream_t s);
+void launch_load_mj_mlp(const Geom &g, int ndim, long long n, int species, unsigned long long seed, int profile,
+                        double L, double x0, double theta, const double beta[3], const void *Wh, int colocate,
+                        Species64 d64, Species64 c64, SpeciesMixed dmx, SpeciesMixed cmx, int mixed, int *err,
+                        cudaStream_t s);
+
 // diag.cu
 template <typename R>
 void launch_field_diag(const Geom &g, FieldPtrs<R> f, double *acc /*6*/, long long *nonfinite, cudaStream_t s);

@@ -1,0 +1,110 @@
+"""Learned inverse-CDF sampler of the loader (method PIC_MJ_MLP): the GPU
+training kernels against the FP64 oracle network, FP16 inference, and the
+trained sampler judged by the exact loader (KS distance and moments) on the
+(theta, beta0) grid of the Harris-sheet workload, next to the naive boost;
+plus the measured gain over the exact inversion."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mj, mlp
+import paper_1308_5892_gb300 as pic
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(precision=pic.PIC_FP64, n=1000, shape=(16, 16, 1), ndim=2):
+    d = pic.run_desc(ndim, shape[0], shape[1], shape[2], 2.0, 16.0, 0.5, [(-1.0, 1.0, n), (1.0, 1.0, n)])
+    return pic.Context([d], precision=precision)
+
+
+def test_training_kernel_gradients_match_oracle():
+    rng = np.random.default_rng(8)
+    p = rng.normal(0, 0.3, mlp.NP).astype(np.float32)
+    x = rng.normal(0, 1, (3, 3000)).astype(np.float32)
+    t = rng.normal(0, 1, 3000).astype(np.float32)
+    with _ctx() as ctx:
+        ctx.mlp_set_weights(p)
+        g, loss = ctx.mlp_gradients(x, t)
+    lo, go = mlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert np.abs(g - go).max() <= 1e-5 * np.abs(go).max()
+
+
+def test_fp16_inference_matches_oracle_forward():
+    rng = np.random.default_rng(9)
+    p = rng.normal(0, 0.2, mlp.NP).astype(np.float32)
+    x = rng.uniform(-1, 1, (3, 5000)).astype(np.float32)
+    with _ctx() as ctx:
+        ctx.mlp_set_weights(p)
+        o = ctx.mlp_infer(x)
+    ref, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64))
+    assert np.abs(o - ref).max() <= 2e-2 * np.abs(ref).max()
+
+
+@pytest.fixture(scope="module")
+def trained():
+    ctx = _ctx(precision=pic.PIC_MIXED, n=400000, shape=(64, 32, 1))
+    loss = ctx.mlp_train(steps=12000, batch=8192, lr=3e-3, seed=1)
+    yield ctx, loss
+    ctx.close()
+
+
+GRID_THETA = np.logspace(-1, 1, 5)
+GRID_BETA = [0.0, 0.3, 0.6, 0.9]
+
+
+def _ks_against_exact(y, theta, beta0):
+    inv = mj.MarginalInverse(theta, beta0)
+    F = inv.cdf_s(np.arcsinh(np.sort(y)))
+    n = len(y)
+    i = np.arange(1, n + 1)
+    return max((i / n - F).max(), (F - (i - 1) / n).max())
+
+
+def test_trained_sampler_ks_and_moments_on_harris_grid(trained):
+    ctx, loss = trained
+    assert loss < 1e-4, loss
+    n = 100000
+    w = mj.uniforms(17, 0, np.arange(n))[3]
+    worst = 0.0
+    for th in GRID_THETA:
+        for b in GRID_BETA:
+            y, _ = ctx.mj_sample_marginal(th, b, w, method=pic.PIC_MJ_MLP)
+            d = _ks_against_exact(y, th, b)
+            worst = max(worst, d)
+            assert d <= 1e-2, (th, b, d)
+    # the naive boost fails the same test where the drift is relativistic
+    wn = mj.uniforms(17, 0, np.arange(n))
+    for th, b in ((1.0, 0.6), (10.0, 0.9)):
+        pn = mj.naive_boost(wn[3], wn[4], wn[5], th, [0.0, 0.0, b])
+        assert _ks_against_exact(pn[2], th, b) > 5 * worst
+    # <gamma> of particles loaded with the learned sampler, against Table averages
+    for th, b in ((0.1, 0.6), (1.0, 0.3), (10.0, 0.9)):
+        ctx.load_maxwell_juttner(0, 0, 100.0, th, (0.0, 0.0, b), method=pic.PIC_MJ_MLP, seed=3)
+        _, counts, _ = ctx.get_state(0, fields_only=True)
+        p = ctx.get_particles(0, 0, np.arange(counts[0]))
+        g = np.sqrt(1 + (p[3:] ** 2).sum(0))
+        assert abs(g.mean() / mj.moments(th, b)["gamma"] - 1) < 0.01, (th, b, g.mean())
+
+
+def test_learned_sampler_gain_over_exact_inversion(trained):
+    """What the network gains: one set of weights serves every (theta, beta0)
+    (no per-parameter table), at a per-sample device cost measured here against
+    the exact table + Newton inversion in FP64."""
+    ctx, loss = trained
+    n = 1 << 22
+    w = mj.uniforms(5, 0, np.arange(n))[3]
+    res = {}
+    for th, b in ((0.1, 0.0), (1.0, 0.6), (10.0, 0.9)):
+        ye, ms_e = ctx.mj_sample_marginal(th, b, w, method=pic.PIC_MJ_EXACT)
+        ym, ms_m = ctx.mj_sample_marginal(th, b, w, method=pic.PIC_MJ_MLP)
+        res["%g,%g" % (th, b)] = {"exact_ms": ms_e, "mlp_ms": ms_m, "speedup": ms_e / ms_m,
+                                  "median_abs_err": float(np.median(np.abs(ym - ye)))}
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open(os.path.join("gpurun_out", "mlp_gain.json"), "w") as f:
+        json.dump(res, f, indent=1)
+    # the learned sampler is not slower than the exact inversion it replaces
+    assert np.median([r["speedup"] for r in res.values()]) > 1.0, res
