@@ -234,6 +234,16 @@ pic_status pic_diagnostics(pic_ctx *ctx, int run, pic_diag *out);
  * *nout receives the number of steps written.  Synchronises. */
 pic_status pic_energy_history(pic_ctx *ctx, int run, double *out, int64_t max_steps, int64_t *nout);
 
+/* Autotuner of the mixed path: advances every run by real steps (at most
+ * max_steps) under each candidate (tile shape, sort interval), keeps the one
+ * with the highest particle-steps per second, and caches it in the process
+ * for contexts of the same shape (a cached choice costs no steps).  The
+ * physical result does not depend on the choice: every particle is advanced
+ * by the same arithmetic and the current is an exact fixed-point sum.
+ * tile, sort_interval (nullable) receive the choice, *steps_taken the number
+ * of steps the trials used.  No-op for PIC_FP64. */
+pic_status pic_autotune(pic_ctx *ctx, int max_steps, int tile[3], int *sort_interval, int *steps_taken);
+
 /* Tuning actually used by a context: tile shape, sort interval, halo. */
 pic_status pic_get_tuning(const pic_ctx *ctx, int tile[3], int *sort_interval, int *halo);
 

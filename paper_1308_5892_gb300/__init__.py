@@ -29,7 +29,7 @@ ABI_FUNCTIONS = [
     "pic_set_uniform_field", "pic_load_maxwell_juttner", "pic_step", "pic_sync", "pic_diagnostics",
     "pic_energy_history", "pic_get_tuning", "pic_get_counters", "pic_kernel_time", "pic_get_particles",
     "pic_mlp_train", "pic_mlp_set_weights", "pic_mlp_get_weights", "pic_mlp_gradients", "pic_mlp_infer",
-    "pic_mj_sample_marginal", "pic_gauss_residual_static",
+    "pic_mj_sample_marginal", "pic_gauss_residual_static", "pic_autotune",
 ]
 MLP_PARAMS = 8641
 
@@ -127,6 +127,8 @@ def lib(build_if_missing=True):
         "pic_mlp_infer": ([P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.POINTER(ctypes.c_float)], st),
         "pic_mj_sample_marginal": ([P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)], st),
+        "pic_autotune": ([P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_int)], st),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -371,3 +373,11 @@ class Context:
         self._check(self._L.pic_mj_sample_marginal(self.h, theta, beta0, _dptr(w), w.size, _dptr(y), method,
                                                     ctypes.byref(ms)))
         return y, ms.value
+
+    def autotune(self, max_steps=200):
+        """Pick tile shape and sort interval on real steps; returns the choice."""
+        t = (ctypes.c_int * 3)()
+        k = ctypes.c_int()
+        n = ctypes.c_int()
+        self._check(self._L.pic_autotune(self.h, max_steps, t, ctypes.byref(k), ctypes.byref(n)))
+        return {"tile": tuple(t), "sort_interval": k.value, "steps_taken": n.value}

@@ -13,6 +13,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -32,6 +34,7 @@ struct SpeciesState {
     int *tile_start = nullptr;  // ntiles + 1, offsets of the current layout
     int *tile_start_alt = nullptr;
     bool tiled = false;         // current layout comes from a sort
+    int tiled_ntiles = 0;       // tile count of the geometry that sort used
 };
 
 struct Run {
@@ -40,6 +43,7 @@ struct Run {
     TileGeom t{};
     int sort_interval = 4;
     int since_sort = 0;
+    int max_tiles = 1;          // tile arrays are sized for the autotuner's smallest tile
     bool sorted = false;
     void *F = nullptr;          // 6 planes of Real (e_x..b_z), padded
     void *J = nullptr;          // 2 buffers x 3 planes, padded: double (FP64) or int64 fixed point (mixed)
@@ -80,6 +84,15 @@ struct pic_ctx {
     std::string err;
     int64_t launches_per_step = 0;
     double bytes_per_ps = 0;
+    // batched ensemble (nruns > 1, mixed): per-run argument tables on the device
+    bool multi = false;
+    MixedStepArgs *multi_args = nullptr;
+    FieldRunF *multi_fe = nullptr, *multi_fp = nullptr;
+    int *multi_tiles = nullptr, *multi_blocks = nullptr, *multi_counter = nullptr;
+    int multi_nblocks = 0;
+    bool multi_tiles_dirty = false;
+    std::vector<MixedStepArgs> h_args;
+    std::vector<FieldRunF> h_fe, h_fp;
     // PIC_FLAG_TIMING: event pairs per kernel class, resolved in pic_kernel_time
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[3];
     std::vector<cudaEvent_t> ev_pool;
@@ -314,36 +327,60 @@ bool validate(const pic_run_desc &d, int precision, std::string &why) {
     return true;
 }
 
-void choose_tiles(Run &r, const pic_opts *o) {
-    const pic_run_desc &d = r.d;
-    int T[3], H;
-    if (d.ndim == 2) { T[0] = 16; T[1] = 16; T[2] = 1; H = 4; }
-    else { T[0] = 8; T[1] = 8; T[2] = 8; H = 3; }
-    if (o) {
-        for (int a = 0; a < 3; ++a)
-            if (o->tile[a] > 0) T[a] = o->tile[a];
+TileGeom make_tile_geom(const pic_run_desc &d, const int Tin[3], int H) {
+    TileGeom t{};
+    const int n3[3] = {d.nx, d.ny, d.ndim == 3 ? d.nz : 1};
+    for (int a = 0; a < 3; ++a) {
+        const int T = (a < d.ndim) ? std::max(1, std::min(Tin[a], n3[a])) : 1;
+        t.T[a] = T;
+        t.R[a] = (a < d.ndim) ? T + 2 * H : 1;
+        t.ntile[a] = (a < d.ndim) ? (n3[a] + T - 1) / T : 1;
     }
-    const int n3[3] = {d.nx, d.ny, d.nz};
-    for (int a = 0; a < d.ndim; ++a) T[a] = std::max(1, std::min(T[a], n3[a]));
-    if (d.ndim == 2) T[2] = 1;
+    t.H = H;
+    t.ntiles = t.ntile[0] * t.ntile[1] * t.ntile[2];
+    t.cells_per_tile = t.T[0] * t.T[1] * t.T[2];
+    return t;
+}
+
+// Candidate tile shapes of the autotuner (the first one is the default).
+std::vector<std::vector<int>> tile_candidates(int ndim) {
+    if (ndim == 2) return {{16, 16, 1}, {32, 16, 1}, {32, 32, 1}, {16, 8, 1}};
+    return {{8, 8, 8}, {8, 8, 4}, {16, 8, 4}};
+}
+std::vector<int> sort_candidates(int ndim) { return ndim == 2 ? std::vector<int>{8, 4, 16} : std::vector<int>{2, 1, 4}; }
+
+void choose_tiles(Run &r, const pic_opts *o, int &max_tiles, long long &max_keys) {
+    const pic_run_desc &d = r.d;
+    int H = d.ndim == 2 ? 4 : 3;
     int hmax = std::min(d.nx, d.ny);
     if (d.ndim == 3) hmax = std::min(hmax, d.nz);
     H = std::max(1, std::min(H, hmax));
-    r.t.H = H;
-    for (int a = 0; a < 3; ++a) {
-        r.t.T[a] = T[a];
-        r.t.R[a] = (a < d.ndim) ? T[a] + 2 * H : 1;
-        r.t.ntile[a] = (a < d.ndim) ? (n3[a] + T[a] - 1) / T[a] : 1;
+    auto cands = tile_candidates(d.ndim);
+    int T[3] = {cands[0][0], cands[0][1], cands[0][2]};
+    const bool user_tile = o && (o->tile[0] > 0 || o->tile[1] > 0 || o->tile[2] > 0);
+    if (user_tile)
+        for (int a = 0; a < 3; ++a)
+            if (o->tile[a] > 0) T[a] = o->tile[a];
+    r.t = make_tile_geom(d, T, H);
+    r.sort_interval = (o && o->sort_interval > 0) ? o->sort_interval : sort_candidates(d.ndim)[0];
+    max_tiles = r.t.ntiles;
+    max_keys = (long long)r.t.ntiles * r.t.cells_per_tile;
+    if (!user_tile) {
+        for (auto &c : cands) {
+            const int Tc[3] = {c[0], c[1], c[2]};
+            const TileGeom t = make_tile_geom(d, Tc, H);
+            max_tiles = std::max(max_tiles, t.ntiles);
+            max_keys = std::max(max_keys, (long long)t.ntiles * t.cells_per_tile);
+        }
     }
-    r.t.ntiles = r.t.ntile[0] * r.t.ntile[1] * r.t.ntile[2];
-    r.t.cells_per_tile = T[0] * T[1] * T[2];
-    r.sort_interval = (o && o->sort_interval > 0) ? o->sort_interval : (d.ndim == 2 ? 8 : 2);
 }
 
 pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     const pic_run_desc &d = r.d;
     const bool mixed = ctx->precision == PIC_MIXED;
-    if (mixed) choose_tiles(r, o);
+    int max_tiles = 1;
+    long long max_keys = 1;
+    if (mixed) choose_tiles(r, o, max_tiles, max_keys);
     const int G = mixed ? r.t.H : 0;
     Geom &g = r.g;
     g.ndim = d.ndim; g.nx = d.nx; g.ny = d.ny; g.nz = d.ndim == 2 ? 1 : d.nz;
@@ -362,10 +399,11 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     if (mixed) {
         r.nfA = (float4 *)dev_alloc(ctx, sizeof(float4) * g.pcells);
         r.nfB = (float2 *)dev_alloc(ctx, sizeof(float2) * g.pcells);
-        const long long nkeys = (long long)r.t.ntiles * r.t.cells_per_tile;
+        const long long nkeys = max_keys;
         r.counts = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.offsets = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.block_sums = (int *)dev_alloc(ctx, sizeof(int) * sort_scan_scratch(nkeys));
+        r.max_tiles = max_tiles;
         int64_t capmax = 1;
         for (int s = 0; s < d.nspecies; ++s) capmax = std::max<int64_t>(capmax, d.species[s].capacity);
         r.perm = (int *)dev_alloc(ctx, sizeof(int) * capmax);
@@ -408,10 +446,10 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
                 }
                 if (!m.cell || !m.id) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for particles");
             }
-            S.tile_start = (int *)dev_alloc(ctx, sizeof(int) * (r.t.ntiles + 1));
-            S.tile_start_alt = (int *)dev_alloc(ctx, sizeof(int) * (r.t.ntiles + 1));
+            S.tile_start = (int *)dev_alloc(ctx, sizeof(int) * (r.max_tiles + 1));
+            S.tile_start_alt = (int *)dev_alloc(ctx, sizeof(int) * (r.max_tiles + 1));
             if (!S.tile_start || !S.tile_start_alt) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for tile offsets");
-            CK(cudaMemsetAsync(S.tile_start, 0, sizeof(int) * (r.t.ntiles + 1), ctx->stream));
+            CK(cudaMemsetAsync(S.tile_start, 0, sizeof(int) * (r.max_tiles + 1), ctx->stream));
         }
     }
     return PIC_OK;
@@ -449,7 +487,8 @@ void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
     a.counts = r.counts;
     a.offsets = r.offsets;
     a.block_sums = r.block_sums;
-    a.old_tile_start = S.tiled ? S.tile_start : nullptr;
+    // the old-tile walk is valid only for the tile geometry the layout was sorted with
+    a.old_tile_start = (S.tiled && S.tiled_ntiles == r.t.ntiles) ? S.tile_start : nullptr;
     a.tile_start = S.tile_start_alt;
     a.perm = r.perm;
     a.err = ctx->d_err;
@@ -457,6 +496,107 @@ void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
     S.cur = 1 - S.cur;
     std::swap(S.tile_start, S.tile_start_alt);
     S.tiled = true;
+    S.tiled_ntiles = r.t.ntiles;
+}
+
+MixedStepArgs mixed_args(pic_ctx *ctx, Run &r, double *hslot) {
+    typedef unsigned long long u64;
+    MixedStepArgs a;
+    a.g = r.g;
+    a.t = r.t;
+    a.nfA = r.nfA;
+    a.nfB = r.nfB;
+    for (int c = 0; c < 3; ++c) a.J[c] = jplane<u64>(r, r.jcur, c);
+    a.nspecies = r.d.nspecies;
+    for (int q = 0; q < r.d.nspecies; ++q) {
+        SpeciesState &S = r.sp[q];
+        a.sp[q] = S.mb[S.cur];
+        a.tile_start[q] = S.tile_start;
+        a.h[q] = (float)S.h;
+        a.sgn[q] = S.q_over_e > 0 ? 1.f : -1.f;
+        a.m_over_me[q] = S.m_over_me;
+    }
+    a.dt = (float)r.d.dt;
+    a.mode = 0;
+    a.kin_acc = hslot;
+    a.err = ctx->d_err;
+    return a;
+}
+
+FieldRunF field_run(Run &r, double *energy) {
+    typedef unsigned long long u64;
+    FieldRunF fr;
+    fr.g = r.g;
+    fr.f = fields_of<float>(r);
+    fr.nfA = r.nfA;
+    fr.nfB = r.nfB;
+    for (int c = 0; c < 3; ++c) {
+        fr.J[c] = jplane<u64>(r, r.jcur, c);
+        fr.Z[c] = jplane<u64>(r, 1 - r.jcur, c);
+    }
+    fr.energy_acc = energy;
+    fr.scale = 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0) * 0x1p-36;
+    return fr;
+}
+
+// One step of every run of a mixed ensemble: per-run sorts when due, then one
+// batched launch per field phase and one persistent push launch for all runs.
+pic_status step_multi(pic_ctx *ctx) {
+    cudaStream_t s = ctx->stream;
+    const int nr = (int)ctx->runs.size();
+    int launches = 0;
+    for (auto &r : ctx->runs) {
+        if (!r.sorted || r.since_sort >= r.sort_interval) {
+            KTimer t(ctx, PIC_KERNEL_SORT);
+            for (int q = 0; q < r.d.nspecies; ++q) sort_species(ctx, r, r.sp[q]);
+            r.sorted = true;
+            r.since_sort = 0;
+            launches += 7 * r.d.nspecies;
+        }
+    }
+    if (ctx->multi_tiles_dirty) {
+        std::vector<int> tp(nr + 1, 0);
+        for (int r = 0; r < nr; ++r) tp[r + 1] = tp[r] + ctx->runs[r].t.ntiles;
+        CK(cudaMemcpyAsync(ctx->multi_tiles, tp.data(), sizeof(int) * (nr + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        ctx->multi_tiles_dirty = false;
+    }
+    for (int i = 0; i < nr; ++i) {
+        Run &r = ctx->runs[i];
+        double *hslot = (r.hist_n < r.hist_cap) ? r.hist + 8 * r.hist_n : nullptr;
+        ctx->h_args[i] = mixed_args(ctx, r, hslot);
+        ctx->h_fe[i] = field_run(r, hslot ? hslot + 2 : nullptr);
+        ctx->h_fp[i] = field_run(r, nullptr);
+    }
+    CK(cudaMemcpyAsync(ctx->multi_args, ctx->h_args.data(), sizeof(MixedStepArgs) * nr, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->multi_fe, ctx->h_fe.data(), sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->multi_fp, ctx->h_fp.data(), sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
+    const float dt = (float)ctx->runs[0].d.dt;
+    {
+        KTimer t(ctx, PIC_KERNEL_FIELD);
+        launch_fields_multi(FIELD_B_HALF, ctx->multi_fe, ctx->multi_blocks, ctx->multi_nblocks, nr, 0.5f * dt, dt, s);
+        launch_fields_multi(FIELD_NODE, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, 0.5f * dt, dt, s);
+    }
+    {
+        KTimer t(ctx, PIC_KERNEL_PUSH);
+        CK(cudaMemsetAsync(ctx->multi_counter, 0, sizeof(int), s));
+        launch_push_mixed_multi(ctx->multi_args, ctx->multi_tiles, nr, ctx->runs[0].d.ndim, ctx->runs[0].t,
+                                ctx->multi_counter, s);
+    }
+    {
+        KTimer t(ctx, PIC_KERNEL_FIELD);
+        launch_fields_multi(FIELD_B_HALF, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, 0.5f * dt, dt, s);
+        launch_fields_multi(FIELD_E_FX, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, 0.5f * dt, dt, s);
+    }
+    for (auto &r : ctx->runs) {
+        r.since_sort++;
+        r.jcur = 1 - r.jcur;
+        r.step++;
+        if (r.hist_n < r.hist_cap) r.hist_n++;
+    }
+    ctx->launches_per_step = launches + 5;
+    ctx->bytes_per_ps = ctx->runs[0].d.ndim == 2 ? 48.0 : 56.0;
+    return PIC_OK;
 }
 
 void step_run(pic_ctx *ctx, Run &r) {
@@ -587,6 +727,44 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
         int64_t cap = 0;
         for (int s = 0; s < runs[r].nspecies; ++s) cap = std::max<int64_t>(cap, runs[r].species[s].capacity);
         stage = std::max(stage, 6 * sizeof(double) * (size_t)std::min<int64_t>(cap, 1 << 24));
+    }
+    if (precision == PIC_MIXED && nruns > 1) {
+        // one batched step for all runs: they must share ndim and tile geometry
+        const Run &r0 = ctx->runs[0];
+        for (int r = 1; r < nruns; ++r) {
+            const Run &rr = ctx->runs[r];
+            if (rr.d.ndim != r0.d.ndim || rr.t.H != r0.t.H || rr.t.T[0] != r0.t.T[0] || rr.t.T[1] != r0.t.T[1] ||
+                rr.t.T[2] != r0.t.T[2] || rr.sort_interval != r0.sort_interval) {
+                pic_destroy(ctx);
+                return PIC_EINVAL;
+            }
+        }
+        ctx->multi = true;
+        ctx->multi_args = (MixedStepArgs *)dev_alloc(ctx, sizeof(MixedStepArgs) * nruns);
+        ctx->multi_fe = (FieldRunF *)dev_alloc(ctx, sizeof(FieldRunF) * nruns);
+        ctx->multi_fp = (FieldRunF *)dev_alloc(ctx, sizeof(FieldRunF) * nruns);
+        ctx->multi_tiles = (int *)dev_alloc(ctx, sizeof(int) * (nruns + 1));
+        ctx->multi_blocks = (int *)dev_alloc(ctx, sizeof(int) * (nruns + 1));
+        ctx->multi_counter = (int *)dev_alloc(ctx, sizeof(int));
+        if (!ctx->multi_args || !ctx->multi_fe || !ctx->multi_fp || !ctx->multi_tiles || !ctx->multi_blocks ||
+            !ctx->multi_counter) {
+            pic_destroy(ctx);
+            return PIC_ENOMEM;
+        }
+        std::vector<int> tp(nruns + 1, 0), bp(nruns + 1, 0);
+        for (int r = 0; r < nruns; ++r) {
+            tp[r + 1] = tp[r] + ctx->runs[r].t.ntiles;
+            bp[r + 1] = bp[r] + (int)((ctx->runs[r].g.pcells + 255) / 256);
+        }
+        ctx->multi_nblocks = bp[nruns];
+        if (cudaMemcpy(ctx->multi_tiles, tp.data(), sizeof(int) * (nruns + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->multi_blocks, bp.data(), sizeof(int) * (nruns + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+            pic_destroy(ctx);
+            return PIC_ECUDA;
+        }
+        ctx->h_args.resize(nruns);
+        ctx->h_fe.resize(nruns);
+        ctx->h_fp.resize(nruns);
     }
     stage = std::max<size_t>(stage, 1 << 16);
     ctx->staging_bytes = stage;
@@ -804,8 +982,14 @@ pic_status pic_set_uniform_field(pic_ctx *ctx, int run, const double e0[3], cons
 pic_status pic_step(pic_ctx *ctx, int nsteps) {
     if (!ctx) return PIC_EINVAL;
     if (nsteps < 0) return fail(ctx, PIC_EINVAL, "nsteps must be >= 0");
-    for (int n = 0; n < nsteps; ++n)
-        for (auto &r : ctx->runs) step_run(ctx, r);
+    for (int n = 0; n < nsteps; ++n) {
+        if (ctx->multi) {
+            pic_status st = step_multi(ctx);
+            if (st) return st;
+        } else {
+            for (auto &r : ctx->runs) step_run(ctx, r);
+        }
+    }
     CK(cudaGetLastError());
     if (ctx->flags & PIC_FLAG_ASYNC) return PIC_OK;
     return read_err(ctx);
@@ -892,6 +1076,121 @@ pic_status pic_energy_history(pic_ctx *ctx, int run, double *out, int64_t max_st
         out[4 * q + 3] = out[4 * q + 0] + out[4 * q + 1] + out[4 * q + 2];
     }
     *nout = n;
+    return PIC_OK;
+}
+
+namespace {
+
+struct TuneKey {
+    int nruns, ndim;
+    long long cells, particles;
+    bool operator<(const TuneKey &o) const {
+        if (nruns != o.nruns) return nruns < o.nruns;
+        if (ndim != o.ndim) return ndim < o.ndim;
+        if (cells != o.cells) return cells < o.cells;
+        return particles < o.particles;
+    }
+};
+struct TuneVal {
+    int T[3];
+    int K;
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
+std::mutex g_tune_mutex;
+
+void apply_tuning(pic_ctx *ctx, const int T[3], int K) {
+    for (auto &r : ctx->runs) {
+        const TileGeom t = make_tile_geom(r.d, T, r.t.H);
+        const bool same = t.T[0] == r.t.T[0] && t.T[1] == r.t.T[1] && t.T[2] == r.t.T[2];
+        r.t = t;
+        r.sort_interval = K;
+        if (!same) {
+            r.sorted = false;
+            for (int q = 0; q < r.d.nspecies; ++q) r.sp[q].tiled = false;
+        }
+    }
+    ctx->multi_tiles_dirty = true;
+}
+
+}  // namespace
+
+pic_status pic_autotune(pic_ctx *ctx, int max_steps, int tile[3], int *sort_interval, int *steps_taken) {
+    if (!ctx) return PIC_EINVAL;
+    if (max_steps < 0) return fail(ctx, PIC_EINVAL, "max_steps must be >= 0");
+    int taken = 0;
+    if (ctx->precision == PIC_MIXED) {
+        const int ndim = ctx->runs[0].d.ndim;
+        TuneKey key{(int)ctx->runs.size(), ndim, 0, 0};
+        for (auto &r : ctx->runs) {
+            key.cells += (long long)r.g.nx * r.g.ny * r.g.nz;
+            for (int q = 0; q < r.d.nspecies; ++q) key.particles += r.sp[q].n;
+        }
+        key.particles = key.particles ? (long long)std::llround(std::log2((double)key.particles) * 4) : 0;
+        TuneVal best{};
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mutex);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) { best = it->second; have = true; }
+        }
+        if (!have) {
+            double best_rate = -1.0;
+            long long parts = 0;
+            for (auto &r : ctx->runs)
+                for (int q = 0; q < r.d.nspecies; ++q) parts += r.sp[q].n;
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            for (auto &tc : tile_candidates(ndim)) {
+                for (int K : sort_candidates(ndim)) {
+                    const int n_trial = std::max(2 * K, 4);
+                    if (taken + n_trial > max_steps) break;
+                    const int T[3] = {tc[0], tc[1], tc[2]};
+                    // a candidate whose tiles exceed the allocated tile arrays is skipped
+                    bool fits = true;
+                    for (auto &r : ctx->runs) {
+                        const TileGeom t = make_tile_geom(r.d, T, r.t.H);
+                        if (t.ntiles > r.max_tiles) fits = false;
+                        if (mixed_smem_bytes(t, ndim) > 220 * 1024) fits = false;
+                    }
+                    if (!fits) continue;
+                    apply_tuning(ctx, T, K);
+                    CK(cudaEventRecord(e0, ctx->stream));
+                    const uint32_t f = ctx->flags;
+                    ctx->flags |= PIC_FLAG_ASYNC;
+                    pic_status st = pic_step(ctx, n_trial);
+                    ctx->flags = f;
+                    if (st) return st;
+                    CK(cudaEventRecord(e1, ctx->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    taken += n_trial;
+                    const double rate = (double)parts * n_trial / (ms * 1e6);
+                    if (rate > best_rate) {
+                        best_rate = rate;
+                        best = TuneVal{{T[0], T[1], T[2]}, K};
+                    }
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (best_rate < 0) {   // no trial fitted in max_steps: keep the current choice
+                const Run &r0 = ctx->runs[0];
+                best = TuneVal{{r0.t.T[0], r0.t.T[1], r0.t.T[2]}, r0.sort_interval};
+            } else {
+                std::lock_guard<std::mutex> lk(g_tune_mutex);
+                g_tune_cache[key] = best;
+            }
+        }
+        apply_tuning(ctx, best.T, best.K);
+        pic_status st = read_err(ctx);
+        if (st) return st;
+    }
+    const Run &r0 = ctx->runs[0];
+    if (tile) for (int a = 0; a < 3; ++a) tile[a] = r0.t.T[a];
+    if (sort_interval) *sort_interval = r0.sort_interval;
+    if (steps_taken) *steps_taken = taken;
     return PIC_OK;
 }
 

@@ -55,10 +55,9 @@ __device__ inline void block_accumulate(double (&v)[NV], double *acc) {
 // is given, the interior sums of e^2 and b^2 (after the update) are added to
 // energy_acc[0..5] in FP64.
 template <typename R>
-__global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, double *energy_acc) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+__device__ __forceinline__ void b_advance_cell(const Geom &g, const FieldPtrs<R> &f, R h, long long p, bool energy,
+                                               double (&acc)[6]) {
+    {
         int pi, pj, pk;
         padded_coords(g, p, pi, pj, pk);
         const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
@@ -74,7 +73,7 @@ __global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, double *energy_acc) {
         f.b[0][p] = bx;
         f.b[1][p] = by;
         f.b[2][p] = bz;
-        if (energy_acc && pi == i + g.G && pj == j + g.G && pk == k + g.Gz) {
+        if (energy && pi == i + g.G && pj == j + g.G && pk == k + g.Gz) {
             acc[0] += (double)ex * (double)ex;
             acc[1] += (double)ey * (double)ey;
             acc[2] += (double)ez * (double)ez;
@@ -83,6 +82,14 @@ __global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, double *energy_acc) {
             acc[5] += (double)bz * (double)bz;
         }
     }
+}
+
+template <typename R>
+__global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, double *energy_acc) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride)
+        b_advance_cell<R>(g, f, h, p, energy_acc != nullptr, acc);
     if (energy_acc) block_accumulate<6>(acc, energy_acc);
 }
 
@@ -137,11 +144,11 @@ __global__ void k_e_advance(Geom g, FieldPtrs<R> f, const R *J0, const R *J1, co
 
 // Mixed path: the same update with the fixed-point current (int64, units of
 // 2^-36 of sgn(q) times the volume flux); scale = |alpha| 2^-36.
-__global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long long *J0,
-                               const unsigned long long *J1, const unsigned long long *J2, unsigned long long *Z0,
-                               unsigned long long *Z1, unsigned long long *Z2, float dt, double scale) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+__device__ __forceinline__ void e_fx_cell(const Geom &g, const FieldPtrs<float> &f, const unsigned long long *J0,
+                                          const unsigned long long *J1, const unsigned long long *J2,
+                                          unsigned long long *Z0, unsigned long long *Z1, unsigned long long *Z2,
+                                          float dt, double scale, long long p) {
+    {
         int pi, pj, pk;
         padded_coords(g, p, pi, pj, pk);
         const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
@@ -166,6 +173,14 @@ __global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long l
     }
 }
 
+__global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long long *J0,
+                               const unsigned long long *J1, const unsigned long long *J2, unsigned long long *Z0,
+                               unsigned long long *Z1, unsigned long long *Z2, float dt, double scale) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride)
+        e_fx_cell(g, f, J0, J1, J2, Z0, Z1, Z2, dt, scale, p);
+}
+
 // Staggered value read by the gather; with conductor walls a value located
 // inside the conductor, or a tangential e / normal b on the wall, reads zero.
 __device__ inline float sval(const Geom &g, const float *a, bool xstag, int i, int j, int k) {
@@ -178,9 +193,9 @@ __device__ inline float sval(const Geom &g, const float *a, bool xstag, int i, i
 
 // Node-averaged fields (App. A.3.3) at every padded node: e over its two edge
 // neighbours, b over its four face neighbours.  Stored as {E_x,E_y,E_z,B_x} and {B_y,B_z}.
-__global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nfA, float2 *nfB) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
+__device__ __forceinline__ void node_cell(const Geom &g, const FieldPtrs<float> &f, float4 *nfA, float2 *nfB,
+                                          long long p) {
+    {
         int pi, pj, pk;
         padded_coords(g, p, pi, pj, pk);
         // node coordinate (not wrapped: the conductor masking needs the true x)
@@ -199,6 +214,47 @@ __global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nfA, float2 *n
                         sval(g, f.b[2], true, i - 1, j - 1, k) + sval(g, f.b[2], true, i, j - 1, k));
         nfA[p] = make_float4(E[0], E[1], E[2], B[0]);
         nfB[p] = make_float2(B[1], B[2]);
+    }
+}
+
+__global__ void k_node_fields(Geom g, FieldPtrs<float> f, float4 *nfA, float2 *nfB) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride)
+        node_cell(g, f, nfA, nfB, p);
+}
+
+// Batched over runs: block b belongs to the run r with block_prefix[r] <= b <
+// block_prefix[r+1] and updates 256 padded cells of that run.
+template <int PHASE>
+__global__ void __launch_bounds__(256) k_fields_multi(const FieldRunF *runs, const int *block_prefix, int nruns,
+                                                      float h, float dt) {
+    __shared__ __align__(16) FieldRunF r;
+    __shared__ int run_sh;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nruns;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (block_prefix[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+        }
+        run_sh = lo;
+    }
+    __syncthreads();
+    {
+        const int *src = reinterpret_cast<const int *>(runs + run_sh);
+        int *dst = reinterpret_cast<int *>(&r);
+        for (int q = threadIdx.x; q < (int)(sizeof(FieldRunF) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    const long long p = (long long)(blockIdx.x - block_prefix[run_sh]) * blockDim.x + threadIdx.x;
+    const bool in = p < r.g.pcells;
+    if (PHASE == FIELD_B_HALF) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        if (in) b_advance_cell<float>(r.g, r.f, h, p, r.energy_acc != nullptr, acc);
+        if (r.energy_acc) block_accumulate<6>(acc, r.energy_acc);
+    } else if (PHASE == FIELD_NODE) {
+        if (in) node_cell(r.g, r.f, r.nfA, r.nfB, p);
+    } else {
+        if (in) e_fx_cell(r.g, r.f, r.J[0], r.J[1], r.J[2], r.Z[0], r.Z[1], r.Z[2], dt, r.scale, p);
     }
 }
 
@@ -238,6 +294,13 @@ void launch_e_advance(const Geom &g, FieldPtrs<R> f, const R *const J[3], R *con
 
 void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nfA, float2 *nfB, cudaStream_t s) {
     k_node_fields<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, nfA, nfB);
+}
+
+void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_prefix_dev, int nblocks, int nruns,
+                         float h, float dt, cudaStream_t s) {
+    if (phase == FIELD_B_HALF) k_fields_multi<FIELD_B_HALF><<<nblocks, 256, 0, s>>>(runs_dev, block_prefix_dev, nruns, h, dt);
+    else if (phase == FIELD_NODE) k_fields_multi<FIELD_NODE><<<nblocks, 256, 0, s>>>(runs_dev, block_prefix_dev, nruns, h, dt);
+    else k_fields_multi<FIELD_E_FX><<<nblocks, 256, 0, s>>>(runs_dev, block_prefix_dev, nruns, h, dt);
 }
 
 void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long long *const J[3],

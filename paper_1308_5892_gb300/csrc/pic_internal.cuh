@@ -124,6 +124,24 @@ struct MixedStepArgs {
     int *err;
 };
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
+// persistent launch over the tiles of many runs (same ndim and tile shape)
+void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
+                             const TileGeom &t, int *counter, cudaStream_t s);
+
+// fields.cu, batched over runs: one launch updates every run's grid
+struct FieldRunF {
+    Geom g;
+    FieldPtrs<float> f;
+    float4 *nfA;
+    float2 *nfB;
+    const unsigned long long *J[3];
+    unsigned long long *Z[3];
+    double *energy_acc;     // e^2, b^2 sums of the step (nullable)
+    double scale;           // |alpha| 2^-36
+};
+enum { FIELD_B_HALF = 0, FIELD_NODE = 1, FIELD_E_FX = 2 };
+void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_prefix_dev, int nblocks, int nruns,
+                         float h, float dt, cudaStream_t s);
 void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
                             float h, float dt, cudaStream_t s);
 size_t mixed_smem_bytes(const TileGeom &t, int ndim);

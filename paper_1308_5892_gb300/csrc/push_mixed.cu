@@ -315,12 +315,12 @@ __device__ __forceinline__ void drain_one(const QueueSink<NDIM> &qs, const TileC
     deposit_segment<NDIM, float>(d, D, sgn, sd);
 }
 
-template <int NDIM, int THREADS, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(MixedStepArgs a) {
+// All species of one tile of one run (the body of both launch forms below).
+template <int NDIM, int THREADS>
+__device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile) {
     extern __shared__ float4 smem4[];
     const Geom &g = a.g;
     const TileGeom &T = a.t;
-    const int tile = blockIdx.x;
     const int tx = tile % T.ntile[0];
     const int ty = (tile / T.ntile[0]) % T.ntile[1];
     const int tz = tile / (T.ntile[0] * T.ntile[1]);
@@ -445,6 +445,41 @@ __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(MixedStepArgs a) {
             atomicAdd(a.kin_acc + 1, kin1);
         }
     }
+    __syncthreads();   // shared memory is reused by the next tile of a persistent CTA
+}
+
+// One CTA per tile of one run.
+template <int NDIM, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(MixedStepArgs a) {
+    push_tile<NDIM, THREADS>(a, blockIdx.x);
+}
+
+// Persistent form for a batch of independent runs of uneven size: resident
+// CTAs take (run, tile) work items from one counter until all tiles of all
+// runs are done, so small runs do not leave most of the GPU idle.
+// tile_prefix[r] is the number of tiles of runs 0..r-1.
+template <int NDIM, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedStepArgs *runs, const int *tile_prefix,
+                                                                    int nruns, int *counter) {
+    __shared__ int item_sh;
+    __shared__ __align__(16) MixedStepArgs args_sh;
+    const int total = tile_prefix[nruns];
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_sh;
+        if (item >= total) break;
+        int lo = 0, hi = nruns;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tile_prefix[mid] <= item) lo = mid; else hi = mid;
+        }
+        const int *src = reinterpret_cast<const int *>(runs + lo);
+        int *dst = reinterpret_cast<int *>(&args_sh);
+        for (int q = threadIdx.x; q < (int)(sizeof(MixedStepArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
+        __syncthreads();
+        push_tile<NDIM, THREADS>(args_sh, item - tile_prefix[lo]);
+    }
 }
 
 // Initial staggering (App. A.3.1): u^0 -> u^{-dt/2} by one Boris step of
@@ -484,6 +519,26 @@ void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB,
     const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
     if (g.ndim == 3) k_half_back_mixed<3><<<blocks, 256, 0, s>>>(g, nfA, nfB, sp, n, h, dt);
     else k_half_back_mixed<2><<<blocks, 256, 0, s>>>(g, nfA, nfB, sp, n, h, dt);
+}
+
+template <int NDIM, int THREADS, int MINB>
+void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem,
+                    cudaStream_t s) {
+    auto k = k_push_mixed_multi<NDIM, THREADS, MINB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k<<<std::max(1, per_sm) * sms, THREADS, smem, s>>>(runs, tile_prefix, nruns, counter);
+}
+
+void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
+                             const TileGeom &t, int *counter, cudaStream_t s) {
+    const size_t smem = mixed_smem_bytes(t, ndim);
+    if (ndim == 3) launch_multi_t<3, 512, 1>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+    else launch_multi_t<2, 256, 2>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
 }
 
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s) {
