@@ -36,6 +36,9 @@ WORKLOADS = {
                          nz=64, ppc=32, theta=1.0, n_x=1.0, rho_sp0=64.0, dt=0.5),
     "thermal2d_512": dict(name="2D3V thermal pair plasma 512^2, 50 ppc/species, theta=0.01", ndim=2, nx=512,
                           ny=512, nz=1, ppc=50, theta=0.01, n_x=20.0, rho_sp0=100.0, dt=0.5),
+    "ensemble256": dict(name="256 independent 2D3V thermal pair plasmas, grids 32^2..256^2, ppc/species in {4..256}, "
+                             "theta in [0.01, 1]", ndim=2, nx=0, ny=0, nz=1, ppc=0, theta=0.0, n_x=0.0, rho_sp0=0.0,
+                        dt=0.5, ensemble=256),
     "thermal2d_64": dict(name="2D3V thermal pair plasma 64^2, 16 ppc/species, theta=0.1", ndim=2, nx=64, ny=64, nz=1,
                          ppc=16, theta=0.1, n_x=0.1 ** -0.5, rho_sp0=32.0, dt=0.5),
 }
@@ -48,6 +51,20 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def ensemble_members(count, seed=4):
+    """The ensemble's runs: N_x, N_y uniform in [32, 256], particles per cell
+    per species from {4, 8, ..., 256}, log theta uniform in [log 0.01, 0],
+    n_x = theta^-1/2 (Debye length = cell), rho_sp0 = 2 ppc."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        nx, ny = (int(v) for v in rng.integers(32, 257, 2))
+        ppc = int(rng.choice([4, 8, 16, 32, 64, 128, 256]))
+        theta = float(np.exp(rng.uniform(np.log(0.01), 0.0)))
+        out.append(dict(nx=nx, ny=ny, ppc=ppc, theta=theta, n_x=theta ** -0.5, rho_sp0=2.0 * ppc))
+    return out
 
 
 def _load(ctx, w, seed):
@@ -129,7 +146,10 @@ def _time_oracle_sample(w, steps, seed):
     temperature; returns (particle-steps/ns, seconds, particles, steps, sizes)."""
     import oracle
     sw = dict(w)
-    if w["ndim"] == 3:
+    if w.get("ensemble"):   # one representative member of the ensemble
+        w = sw = dict(ndim=2, nx=64, ny=64, nz=1, ppc=32, theta=0.1, n_x=0.1 ** -0.5, rho_sp0=64.0, dt=0.5,
+                      name=w["name"])
+    elif w["ndim"] == 3:
         sw.update(nx=32, ny=32, nz=32)
     else:
         sw.update(nx=min(w["nx"], 64), ny=min(w["ny"], 64), nz=1)
@@ -183,19 +203,42 @@ def run_ours(args, w):
             dist.barrier()
         torch.cuda.synchronize()
 
-    nz = 1 if w["ndim"] == 2 else w["nz"]
-    n = int(round(w["ppc"] * w["nx"] * w["ny"] * nz))
-    desc = pic.run_desc(w["ndim"], w["nx"], w["ny"], nz, w["n_x"], w["rho_sp0"], w["dt"],
-                        [(-1.0, 1.0, n), (1.0, 1.0, n)])
     seed = 2 + 1000 * rank
-    npart = 2 * n
+    if w.get("ensemble"):
+        members = ensemble_members(w["ensemble"])
+        descs = []
+        npart = 0
+        for m in members:
+            n = m["ppc"] * m["nx"] * m["ny"]
+            npart += 2 * n
+            descs.append(pic.run_desc(2, m["nx"], m["ny"], 1, m["n_x"], m["rho_sp0"], w["dt"],
+                                      [(-1.0, 1.0, n), (1.0, 1.0, n)]))
+    else:
+        members = None
+        nz = 1 if w["ndim"] == 2 else w["nz"]
+        n = int(round(w["ppc"] * w["nx"] * w["ny"] * nz))
+        descs = [pic.run_desc(w["ndim"], w["nx"], w["ny"], nz, w["n_x"], w["rho_sp0"], w["dt"],
+                              [(-1.0, 1.0, n), (1.0, 1.0, n)])]
+        npart = 2 * n
+
+    def load_all(ctx):
+        if members is None:
+            _load(ctx, w, seed)
+        else:
+            for r, m in enumerate(members):
+                ctx.load_maxwell_juttner(r, 0, m["ppc"], m["theta"], (0.0, 0.0, 0.0), seed=seed + 2 * r)
+                ctx.load_maxwell_juttner(r, 1, m["ppc"], m["theta"], (0.0, 0.0, 0.0), colocate_with=0,
+                                         seed=seed + 2 * r + 1)
     results = {}
     legs = ((pic.PIC_MIXED, "mixed"),) if args.no_fp64 else ((pic.PIC_MIXED, "mixed"), (pic.PIC_FP64, "fp64"))
     for prec, name in legs:
         steps = args.steps if prec == pic.PIC_MIXED else max(1, min(args.steps, args.fp64_steps))
-        ctx = pic.Context([desc], precision=prec, flags=pic.PIC_FLAG_TIMING, tile=tuple(args.tile),
+        ctx = pic.Context(descs, precision=prec, flags=pic.PIC_FLAG_TIMING, tile=tuple(args.tile),
                           sort_interval=args.sort_interval)
-        _load(ctx, w, seed)
+        load_all(ctx)
+        tuned = None
+        if prec == pic.PIC_MIXED and not args.no_autotune and args.tile == (0, 0, 0) and args.sort_interval == 0:
+            tuned = ctx.autotune(max_steps=args.autotune_steps)
         ctx.step(args.warmup)
         ctx.kernel_time(pic.PIC_KERNEL_PUSH, reset=True)
         stream = torch.cuda.current_stream()
@@ -222,7 +265,7 @@ def run_ours(args, w):
             ms = float(t.item())
         results[name] = dict(ms=ms, steps=steps, push_ms=push_ms, push_n=push_n, field_ms=field_ms,
                              sort_ms=sort_ms, counters=cnt, clocks=clk, diag=diag,
-                             tuning=ctx.tuning() if prec == pic.PIC_MIXED else None)
+                             tuning=dict(ctx.tuning(), autotune=tuned) if prec == pic.PIC_MIXED else None)
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
@@ -231,11 +274,11 @@ def run_ours(args, w):
     # timed steps, read the state back; all copies inside the timed region
     e2e_s = None
     h2d = d2h = 0
-    if not args.no_e2e:
-        e2e_s, h2d, d2h = _e2e(pic, torch, desc, w, seed, args, barrier)
+    if not args.no_e2e and members is None:
+        e2e_s, h2d, d2h = _e2e(pic, torch, descs[0], w, seed, args, barrier)
     if args.no_fp64:
         results["fp64"] = None
-    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist)
+    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, len(descs))
 
 
 def _e2e(pic, torch, desc, w, seed, args, barrier):
@@ -263,7 +306,7 @@ def _e2e(pic, torch, desc, w, seed, args, barrier):
     return e2e_s, nbytes, nbytes
 
 
-def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist):
+def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1):
     m = results["mixed"]
     value_rank = npart * m["steps"] / (m["ms"] * 1e6)
     value = value_rank * world
@@ -278,7 +321,7 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / m["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32 (mixed); f64",
             "data": "synthetic",
-            "config": {"workload": w["name"], "particles_per_gpu": npart, "cells": w["nx"] * w["ny"] * (w["nz"] if w["ndim"] == 3 else 1),
+            "config": {"workload": w["name"], "particles_per_gpu": npart, "runs": nruns,
                        "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 (%.1f GB particle state)" % (npart * 28 / 1e9),
                        "tuning": m["tuning"]},
             "fp64": None if f64 is None else {"value": npart * f64["steps"] / (f64["ms"] * 1e6) * world,
@@ -321,7 +364,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--tile", type=int, nargs=3, default=(0, 0, 0))
     ap.add_argument("--sort-interval", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-steps", type=int, default=120)
     args = ap.parse_args()
+    args.tile = tuple(args.tile)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
