@@ -11,6 +11,12 @@ namespace pic {
 template <typename R> __device__ inline R rsqrt_(R x);
 template <> __device__ inline float rsqrt_<float>(float x) { return rsqrtf(x); }
 template <> __device__ inline double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+// Division: IEEE in FP64; in FP32 the fast reciprocal-based quotient (2 ulp for
+// divisors in [2^-126, 2^126], which every divisor here is), far below the
+// FP32 rounding of the arguments themselves.
+template <typename R> __device__ inline R div_(R a, R b);
+template <> __device__ inline float div_<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ inline double div_<double>(double a, double b) { return a / b; }
 
 // Boris step with h = (q/e)(m_e/m), fields E, B at the particle:
 //   u- = u + h E dt/2;  gamma = sqrt(1 + u-^2);  t = h B dt/(2 gamma);
@@ -24,7 +30,7 @@ __device__ inline void boris(R u[3], const R E[3], const R B[3], R h, R dt) {
     const R inv_gam = rsqrt_<R>(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
     const R qb = qe * inv_gam;
     const R t[3] = {qb * B[0], qb * B[1], qb * B[2]};
-    const R f = R(2) / (R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const R f = div_<R>(R(2), R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     const R s[3] = {f * t[0], f * t[1], f * t[2]};
     const R up[3] = {um[0] + (um[1] * t[2] - um[2] * t[1]), um[1] + (um[2] * t[0] - um[0] * t[2]),
                      um[2] + (um[0] * t[1] - um[1] * t[0])};
@@ -88,78 +94,98 @@ __device__ __forceinline__ void deposit_segment(const R d[3], const R D[3], R al
 // a shift s[a] in {-1,0,1} cells and the end offset d1[a] in the end cell.  The
 // path is split at the node planes it crosses (at most one per axis); the
 // pieces are taken in increasing crossing parameter, ties in axis order, and
-// each piece is deposited in its own cell by deposit_segment.  Positions at
-// the breakpoints are the exact plane values and the stored end, so the
-// segment displacements telescope to the stored total and charge is conserved
-// up to the rounding of the fluxes.  dz2d is the out-of-plane displacement in
-// 2D3V, shared between the pieces in proportion to their parameter length.
-// sink.piece(k, di, dj, dk, d, D, alpha) receives piece k, its cell offset from
-// the start cell, its start offset d and displacement D; PieceDeposit below
-// deposits it at once.
-template <int NDIM, typename R, class Sink>
-__device__ __forceinline__ void deposit_path(const R d0[3], const int s[3], const R d1[3], R dz2d, R alpha,
-                                             Sink &sink) {
-    R tc[3], dv[3], plo[3], pnew[3];
-    int ncross = 0;
+// each piece lies in its own cell.  Positions at the breakpoints are the exact
+// plane values and the stored end, so the piece displacements telescope to the
+// stored total and charge is conserved up to the rounding of the fluxes.  dz2d
+// is the out-of-plane displacement in 2D3V, shared between the pieces in
+// proportion to their parameter length.
+// init() sets up the split; piece(k, ...) must then be called for k = 0, 1, ...,
+// ncross in this order and returns piece k: its cell offset from the start
+// cell, its start offset and its displacement.
+template <int NDIM, typename R>
+struct PathSplit {
+    R cur[3], dv[3], tc[3], d1[3];
+    int code;     // per axis a, bits 4a..4a+3: (s[a] + 1) | rank[a] << 2, rank 3 if the axis is not crossed
+    int ncross;
+    R tprev, dz;
+    __device__ __forceinline__ int sh(int a) const { return ((code >> (4 * a)) & 3) - 1; }
+    __device__ __forceinline__ int rk(int a) const { return (code >> (4 * a + 2)) & 3; }
+    __device__ __forceinline__ R plo(int a) const { return sh(a) > 0 ? R(1) : R(0); }   // plane, start-cell coords
+    __device__ __forceinline__ R pnew(int a) const { return sh(a) > 0 ? R(0) : R(1); }  // same plane, end-cell coords
+    __device__ __forceinline__ void init(const R d0[3], const int s[3], const R d1_[3], R dz2d) {
+        ncross = 0;
+        code = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        tc[a] = R(2);
-        dv[a] = R(0);
-        plo[a] = R(0);
-        pnew[a] = R(0);
-        if (a < NDIM) {
-            plo[a] = s[a] > 0 ? R(1) : R(0);   // crossing plane in start-cell coordinates
-            pnew[a] = s[a] > 0 ? R(0) : R(1);  // the same plane in end-cell coordinates
-            if (s[a] != 0) {
-                const R first = plo[a] - d0[a];
-                dv[a] = first + (d1[a] - pnew[a]);
-                tc[a] = dv[a] != R(0) ? first / dv[a] : R(0);
-                ++ncross;
-            } else {
-                dv[a] = d1[a] - d0[a];
+        for (int a = 0; a < 3; ++a) {
+            cur[a] = a < NDIM ? d0[a] : R(0);
+            d1[a] = a < NDIM ? d1_[a] : R(0);
+            tc[a] = R(2);
+            dv[a] = R(0);
+            const int sa = a < NDIM ? s[a] : 0;
+            code |= (sa + 1) << (4 * a);
+            if (a < NDIM) {
+                if (sa != 0) {
+                    const R first = (sa > 0 ? R(1) : R(0)) - cur[a];
+                    dv[a] = first + (d1[a] - (sa > 0 ? R(0) : R(1)));
+                    tc[a] = dv[a] != R(0) ? div_<R>(first, dv[a]) : R(0);
+                    ++ncross;
+                } else {
+                    dv[a] = d1[a] - cur[a];
+                }
             }
         }
-    }
-    // rank of each axis' crossing (non-crossing axes rank last), ties by axis order
-    int rank[3];
+        // rank of each crossing among the crossings, ties by axis order
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        rank[a] = 0;
+        for (int a = 0; a < 3; ++a) {
+            int r = 3;
+            if (a < NDIM && sh(a) != 0) {
+                r = 0;
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            if (b != a && b < NDIM && a < NDIM && (tc[b] < tc[a] || (tc[b] == tc[a] && b < a))) ++rank[a];
+                for (int b = 0; b < NDIM; ++b)
+                    if (b != a && sh(b) != 0 && (tc[b] < tc[a] || (tc[b] == tc[a] && b < a))) ++r;
+            }
+            code |= r << (4 * a + 2);
+        }
+        tprev = R(0);
+        dz = dz2d;
     }
-    R cur[3] = {d0[0], d0[1], NDIM == 3 ? d0[2] : R(0)};
-    int cs[3] = {0, 0, 0};
-    R tprev = R(0);
-    // one rolled loop over the pieces keeps a single copy of the deposit in the
-    // instruction stream; every array below is still indexed by unrolled axes
-#pragma unroll 1
-    for (int k = 0; k <= ncross; ++k) {
+    __device__ __forceinline__ void piece(int k, int c[3], R d[3], R D[3]) {
         R tn = R(1);
 #pragma unroll
         for (int a = 0; a < NDIM; ++a)
-            if (s[a] != 0 && rank[a] == k) tn = tc[a];
+            if (rk(a) == k) tn = tc[a];
         const bool last = (k == ncross);
-        R D[3], endp[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (a >= NDIM) { endp[a] = R(0); D[a] = R(0); continue; }
-            const bool cx = s[a] != 0;
-            if (cx && rank[a] == k) endp[a] = plo[a];
-            else if (last) endp[a] = d1[a];
-            else if (cx && rank[a] < k) endp[a] = pnew[a] + dv[a] * (tn - tc[a]);
-            else endp[a] = d0[a] + dv[a] * tn;
-            D[a] = endp[a] - cur[a];
+            c[a] = rk(a) < k ? sh(a) : 0;
+            d[a] = cur[a];
+            if (a >= NDIM) { D[a] = R(0); continue; }
+            R endp;
+            if (rk(a) == k) endp = plo(a);
+            else if (last) endp = d1[a];
+            else endp = cur[a] + dv[a] * (tn - tprev);
+            D[a] = endp - cur[a];
+            cur[a] = rk(a) == k ? pnew(a) : endp;
         }
-        if (NDIM == 2) D[2] = dz2d * (tn - tprev);
-        sink.piece(k, cs[0], cs[1], cs[2], cur, D, alpha);
-#pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            cur[a] = endp[a];
-            if (s[a] != 0 && rank[a] == k) { cur[a] = pnew[a]; cs[a] = s[a]; }
-        }
+        if (NDIM == 2) D[2] = dz * (tn - tprev);
         tprev = tn;
+    }
+};
+
+// All pieces of the path, in order: sink.piece(k, di, dj, dk, d, D, alpha).
+template <int NDIM, typename R, class Sink>
+__device__ __forceinline__ void deposit_path(const R d0[3], const int s[3], const R d1[3], R dz2d, R alpha,
+                                             Sink &sink) {
+    PathSplit<NDIM, R> ps;
+    ps.init(d0, s, d1, dz2d);
+    // one rolled loop over the pieces keeps a single copy of the deposit in the
+    // instruction stream; every array is still indexed by unrolled axes
+#pragma unroll 1
+    for (int k = 0; k <= ps.ncross; ++k) {
+        int c[3];
+        R d[3], D[3];
+        ps.piece(k, c, d, D);
+        sink.piece(k, c[0], c[1], c[2], d, D, alpha);
     }
 }
 

@@ -6,28 +6,36 @@
 //  - node fields E, B at time t (App. A.3.3 averages, computed once per step
 //    by the field kernels) for the R^d nodes of the tile + halo are staged in
 //    shared memory as one float4 {E_x,E_y,E_z,B_x} and one float2 {B_y,B_z}
-//    per node; particles are sorted by cell inside the tile, so the lanes of a
-//    warp mostly read the same node (broadcast);
+//    per node;
 //  - the current of the tile + halo is accumulated in shared memory in exact
-//    fixed point: each flux v (units of the particle volume times sgn q) is
-//    rounded to a multiple of 2^-36 and split into two int32 limbs, v*2^18
-//    rounded (hi) and the remainder times 2^18 rounded (lo), added with
-//    integer atomics.  GB300 resolves same-address integer atomics of a warp
-//    at full rate, whereas FP32 shared atomics serialise on conflicts (which
-//    cell-sorted lanes cause on every deposit).  Integer sums are exact and
-//    associative, so the current is independent of the order of the
-//    particles; at the end hi*2^18 + lo is added once per node to the global
-//    int64 current;
+//    fixed point.  Every flux v (units of the particle volume times sgn q;
+//    |v| < 1 because |D| < dt < 1) is rounded once, x = rint(v 2^26), an
+//    int32, and x is added as two int32 limbs, hi += x >> 8 and lo += x & 255,
+//    so neither limb overflows however many particles a node collects.
+//    Integer sums are exact and associative, so the current does not depend
+//    on the order of the particles, on the tiling or on the sort interval.  At
+//    the end hi 2^18 + lo 2^10 (units 2^-36) is added once per node to the
+//    global int64 current.  The rounding, 2^-27 at most per flux, is below the
+//    FP32 rounding of the flux itself.  (FP32 shared atomics would serialise
+//    on the address conflicts that cell-sorted particles cause on every
+//    deposit; integer atomics and the register accumulation below avoid that.)
 //  - particles (packed cell, FP32 offsets, FP32 momenta) are streamed once:
-//    read 24 B (2D) / 28 B (3D) and write the same.
+//    read 24 B (2D) / 28 B (3D) and written back.  Each warp prefetches the
+//    particles of its next iterations with cp.async into a ring of
+//    shared-memory stages, so the DRAM latency overlaps the arithmetic.
+// Work of a warp: 1024-particle blocks, which the sort stores 32 x 32
+// transposed, so lane a walks 32 consecutive cell-sorted particles (and keeps
+// their start-cell current in registers until its cell changes) while one
+// load instruction still reads one contiguous 128-byte row.  The pieces of a
+// path after a node-plane crossing are queued per warp and deposited 32 at a
+// time by all lanes together.
 // A particle whose stencil leaves the staged box (it drifted far since the
 // last sort) takes a slow path that gathers from global memory and deposits
 // with global int64 atomics of the same fixed-point values, so the result
 // never depends on the sort interval.
 //
-// Roofline: HBM bound.  Algorithmic bytes per particle-step = 2 x 24 B (2D) or
-// 2 x 28 B (3D); field and current traffic per cell is amortised over the
-// particles per cell.
+// Roofline: HBM bound at 2 x 24 B (2D) or 2 x 28 B (3D) per particle-step;
+// field and current traffic per cell is amortised over the particles per cell.
 #include <algorithm>
 
 #include "particle_core.cuh"
@@ -37,34 +45,22 @@ namespace pic {
 
 namespace {
 
-constexpr float kFx1 = 262144.0f;   // 2^18: scale of the hi limb and of the lo remainder
+constexpr float kFx26 = 67108864.0f;   // 2^26: fixed-point scale of one flux
+constexpr unsigned kFull = 0xffffffffu;
 
-// Shared-memory current sink, two int32 fixed-point limbs per value.
-struct SmemSinkFx {
-    int *hi, *lo;
-    int sx, sxy, nodes;
-    int base0, base;
-    __device__ __forceinline__ void set_cell(int di, int dj, int dk) { base = base0 + di + dj * sx + dk * sxy; }
-    __device__ __forceinline__ void operator()(int comp, int di, int dj, int dk, float v) {
-        const int q = comp * nodes + base + di + dj * sx + dk * sxy;
-        const float x = v * kFx1;
-        const float h = rintf(x);
-        atomicAdd(hi + q, (int)h);
-        atomicAdd(lo + q, __float2int_rn((x - h) * kFx1));
-    }
-};
+// The fixed-point value of one flux (see the header comment).
+__device__ __forceinline__ int fx(float v) { return __float2int_rn(v * kFx26); }
 
 // Global current sink for particles outside the staged box: the same
-// fixed-point value, added as one int64 at the interior-wrapped padded index.
+// fixed-point value in units 2^-36, added as one int64 at the interior-wrapped
+// padded index.
 struct GlobalSinkFx {
     const Geom *g;
     unsigned long long *J[3];
     int ci, cj, ck, oi, oj, ok;
     __device__ void set_cell(int di, int dj, int dk) { oi = ci + di; oj = cj + dj; ok = ck + dk; }
     __device__ void operator()(int comp, int di, int dj, int dk, float v) {
-        const float x = v * kFx1;
-        const float h = rintf(x);
-        const long long f = (long long)h * 262144LL + (long long)__float2int_rn((x - h) * kFx1);
+        const long long f = (long long)fx(v) * 1024LL;
         atomicAdd(J[comp] + g->widx(oi + di, oj + dj, ok + dk), (unsigned long long)f);
     }
 };
@@ -122,111 +118,90 @@ __device__ __noinline__ void gather_global(const Geom &g, const float4 *nA, cons
             }
 }
 
-// Kahan-compensated FP32 running sum (per thread).
-struct KahanF {
-    float s = 0.f, c = 0.f;
-    __device__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-
-// First-segment currents of consecutive particles of one thread that start in
-// the same cell, accumulated exactly in registers (the same two fixed-point
-// limbs as the shared-memory sink) and added to shared memory once per cell.
-// Value index: 3D comp 0 (dj + 2dk), comp 1 4 + (di + 2dk), comp 2 8 + (di + 2dj);
+// Value index of a start-cell flux in the register accumulator:
+// 3D comp 0 (dj + 2dk), comp 1 4 + (di + 2dk), comp 2 8 + (di + 2dj);
 // 2D comp 0 dj, comp 1 2 + di, comp 2 4 + (di + 2dj).
+template <int NDIM>
+__device__ __forceinline__ int acc_index(int comp, int di, int dj, int dk) {
+    if (NDIM == 3) return comp == 0 ? dj + 2 * dk : (comp == 1 ? 4 + di + 2 * dk : 8 + di + 2 * dj);
+    return comp == 0 ? dj : (comp == 1 ? 2 + di : 4 + di + 2 * dj);
+}
+template <int NDIM>
+__device__ __forceinline__ void acc_offset(int v, int &comp, int &di, int &dj, int &dk) {
+    di = dj = dk = 0;
+    if (NDIM == 3) {
+        comp = v / 4;
+        const int r = v % 4;
+        if (comp == 0) { dj = r & 1; dk = r >> 1; }
+        else if (comp == 1) { di = r & 1; dk = r >> 1; }
+        else { di = r & 1; dj = r >> 1; }
+    } else {
+        if (v < 2) { comp = 0; dj = v; }
+        else if (v < 4) { comp = 1; di = v - 2; }
+        else { comp = 2; di = (v - 4) & 1; dj = (v - 4) >> 1; }
+    }
+}
+
+// Start-cell fluxes of consecutive particles of one lane that start in the
+// same cell, summed exactly in registers (units 2^-26; at most 32 particles of
+// |v| < 1 each, so no overflow) and added to shared memory once per cell.
 template <int NDIM>
 struct RegAcc {
     static constexpr int NV = NDIM == 3 ? 12 : 8;
-    int hi[NV], lo[NV];
+    int x[NV];
     int q0;   // local node index of the accumulation cell, -1 when empty
     __device__ __forceinline__ void reset(int q) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { hi[v] = 0; lo[v] = 0; }
+        for (int v = 0; v < NV; ++v) x[v] = 0;
         q0 = q;
     }
-    __device__ __forceinline__ static int index(int comp, int di, int dj, int dk) {
-        if (NDIM == 3) return comp == 0 ? dj + 2 * dk : (comp == 1 ? 4 + di + 2 * dk : 8 + di + 2 * dj);
-        return comp == 0 ? dj : (comp == 1 ? 2 + di : 4 + di + 2 * dj);
+    __device__ __forceinline__ void operator()(int comp, int di, int dj, int dk, float v) {
+        x[acc_index<NDIM>(comp, di, dj, dk)] += fx(v);
     }
     __device__ __forceinline__ void flush(int *Jhi, int *Jlo, int nodes, int sx, int sxy) {
         if (q0 < 0) return;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            int comp, di = 0, dj = 0, dk = 0;
-            if (NDIM == 3) {
-                comp = v / 4;
-                const int r = v % 4;
-                if (comp == 0) { dj = r & 1; dk = r >> 1; }
-                else if (comp == 1) { di = r & 1; dk = r >> 1; }
-                else { di = r & 1; dj = r >> 1; }
-            } else {
-                if (v < 2) { comp = 0; dj = v; }
-                else if (v < 4) { comp = 1; di = v - 2; }
-                else { comp = 2; di = (v - 4) & 1; dj = (v - 4) >> 1; }
-            }
+            int comp, di, dj, dk;
+            acc_offset<NDIM>(v, comp, di, dj, dk);
             const int q = comp * nodes + q0 + di + dj * sx + dk * sxy;
-            atomicAdd(Jhi + q, hi[v]);
-            atomicAdd(Jlo + q, lo[v]);
+            atomicAdd(Jhi + q, x[v] >> 8);
+            atomicAdd(Jlo + q, x[v] & 255);
         }
         q0 = -1;
     }
 };
 
-// Per-warp ring buffer of path pieces waiting to be deposited (128 entries):
-// local node index of the piece's cell, start offset and displacement.
-constexpr int kQueue = 128;
-struct PieceQueue {
-    int *base;      // [kQueue]
-    float *d;       // [3][kQueue]
-    float *D;       // [3][kQueue]
-    int *count;     // pieces waiting (shared, per warp)
+// Shared-memory value sink of queued pieces: both limbs with integer atomics.
+struct SmemSinkFx {
+    int *hi, *lo;
+    int sx, sxy, nodes, base;
+    __device__ __forceinline__ void operator()(int comp, int di, int dj, int dk, float v) {
+        const int q = comp * nodes + base + di + dj * sx + dk * sxy;
+        const int x = fx(v);
+        atomicAdd(hi + q, x >> 8);
+        atomicAdd(lo + q, x & 255);
+    }
 };
 
-// Piece sink of the fast path: the piece in the start cell goes to the
-// register accumulator; pieces in the neighbour cells (after a node-plane
-// crossing) are appended to the warp's queue, so that they are deposited
-// later by all 32 lanes together instead of by the few crossing lanes.
+// cp.async of one 4-byte word, global -> shared, and its group fences.
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void *gptr) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(__cvta_generic_to_global(gptr))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kQueue = 64;      // per-warp ring of waiting pieces (at most 63 wait at any time)
+constexpr int kStages = 3;      // per-warp particle prefetch ring
+template <int NDIM> __host__ __device__ constexpr int words_per_particle() { return NDIM == 3 ? 7 : 6; }
+
+// Shared memory of one warp after the node fields and the current limbs: the
+// piece queue (cell base, d[3], D[3]: 7 x kQueue words) and the particle
+// stages (kStages x words_per_particle x 32 words).
 template <int NDIM>
-struct QueueSink {
-    RegAcc<NDIM> *acc;
-    PieceQueue q;
-    int qhead;      // warp-uniform ring position of the oldest waiting piece
-    int q0, sx, sxy;
-    __device__ __forceinline__ void set_cell(int, int, int) {}
-    // value sink used for the start-cell piece
-    __device__ __forceinline__ void operator()(int comp, int di, int dj, int dk, float v) {
-        const float x = v * kFx1;
-        const float h = rintf(x);
-        const int k = RegAcc<NDIM>::index(comp, di, dj, dk);
-        acc->hi[k] += (int)h;
-        acc->lo[k] += __float2int_rn((x - h) * kFx1);
-    }
-    __device__ __forceinline__ void piece(int k, int di, int dj, int dk, const float d[3], const float D[3],
-                                          float alpha) {
-        if (k == 0) {
-            deposit_segment<NDIM, float>(d, D, alpha, *this);
-            return;
-        }
-        // lanes appending together reserve consecutive slots with one atomic
-        const unsigned mask = __activemask();
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(mask) - 1;
-        int start = 0;
-        if (lane == leader) start = atomicAdd(q.count, __popc(mask));
-        start = __shfl_sync(mask, start, leader);
-        const int idx = (qhead + start + __popc(mask & ((1u << lane) - 1u))) & (kQueue - 1);
-        q.base[idx] = q0 + di + dj * sx + dk * sxy;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            q.d[a * kQueue + idx] = d[a];
-            q.D[a * kQueue + idx] = D[a];
-        }
-    }
-};
+__host__ __device__ constexpr int warp_smem_words() { return 7 * kQueue + kStages * words_per_particle<NDIM>() * 32; }
 
 // Per-CTA constants of the tile.
 struct TileCtx {
@@ -236,16 +211,16 @@ struct TileCtx {
     int *Jhi, *Jlo;
 };
 
-// One particle: gather, Boris, move, deposit.  c/d/u are updated in place.
-// With ACC the start-cell piece of the path goes to the register accumulator.
+// Gather, Boris and move of one particle.  On return c, d, u hold the new
+// state; d0, s, D describe the path for the deposit; fast tells whether the
+// stencil stays in the staged box, and q0 is then the local node index of the
+// start cell.
 template <int NDIM>
-__device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &tc, QueueSink<NDIM> &qs, float h,
-                                         float sgn, uint32_t &cell, float d[3], float u[3], KahanF &k0,
-                                         KahanF &k1) {
-    RegAcc<NDIM> &acc = *qs.acc;
+__device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &tc, float h, uint32_t &c, float d[3],
+                                         float u[3], float d0[3], int s[3], float D[3], bool &fast, int &q0,
+                                         int &ci, int &cj, int &ck, float &kin0, float &kin1) {
     const Geom &g = a.g;
-    int ci, cj, ck;
-    unpack_cell(NDIM, cell, ci, cj, ck);
+    unpack_cell(NDIM, c, ci, cj, ck);
     // local cell in the staged box, nearest periodic image of the tile
     int lx = ci - tc.x0, ly = cj - tc.y0, lz = NDIM == 3 ? ck - tc.z0 : 0;
     if (lx >= tc.T0 + tc.H) lx -= g.nx; else if (lx < -tc.H) lx += g.nx;
@@ -254,10 +229,10 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
     lx += tc.H; ly += tc.H; lz += NDIM == 3 ? tc.H : 0;
     // fast path: the gather reads nodes l..l+1 and the deposit writes nodes
     // l-1..l+2 of the staged box, all of which must also lie in the padded grid
-    bool fast = lx >= 1 && lx <= tc.Rx - 3 && ly >= 1 && ly <= tc.Ry - 3 && tc.x0 + lx + 2 < g.px &&
-                tc.y0 + ly + 2 < g.py;
+    fast = lx >= 1 && lx <= tc.Rx - 3 && ly >= 1 && ly <= tc.Ry - 3 && tc.x0 + lx + 2 < g.px &&
+           tc.y0 + ly + 2 < g.py;
     if (NDIM == 3) fast = fast && lz >= 1 && lz <= tc.Rz - 3 && tc.z0 + lz + 2 < g.pz;
-    const int q0 = lx + ly * tc.sx + lz * tc.sxy;
+    q0 = lx + ly * tc.sx + lz * tc.sxy;
     float E[3], B[3];
     if (fast) gather_nodes<NDIM>(tc.nA, tc.nB, q0, tc.sx, tc.sxy, d, E, B);
     else gather_global<NDIM>(g, a.nfA, a.nfB, ci, cj, ck, d, E, B);
@@ -267,11 +242,14 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
     const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const float inv_gam = rsqrtf(1.f + u2);
     // gamma - 1 = u^2 / (1 + gamma), free of cancellation
-    k0.add(u2_0 / (1.f + sqrtf(1.f + u2_0)));
-    k1.add(u2 / (1.f + 1.f / inv_gam));
-    const float D[3] = {dt * u[0] * inv_gam, dt * u[1] * inv_gam, dt * u[2] * inv_gam};
-    int s[3] = {0, 0, 0};
-    float d1[3] = {0.f, 0.f, 0.f};
+    kin0 += __fdividef(u2_0, 1.f + (1.f + u2_0) * rsqrtf(1.f + u2_0));
+    kin1 += __fdividef(u2, 1.f + (1.f + u2) * inv_gam);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        D[ax] = dt * u[ax] * inv_gam;
+        d0[ax] = d[ax];
+        s[ax] = 0;
+    }
 #pragma unroll
     for (int ax = 0; ax < NDIM; ++ax) {
         const float pa = d[ax] + D[ax];
@@ -284,34 +262,21 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
             da = d[ax];
         }
         s[ax] = (int)sa;
-        d1[ax] = da;
-    }
-    if (fast) {
-        if (acc.q0 != q0) {
-            acc.flush(tc.Jhi, tc.Jlo, tc.nodes, tc.sx, tc.sxy);
-            acc.reset(q0);
-        }
-        qs.q0 = q0;
-        deposit_path<NDIM, float>(d, s, d1, D[2], sgn, qs);
-    } else {
-        deposit_global<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d, s, d1, D[2], sgn);
+        d[ax] = da;
     }
     const int ni = g.wx(ci + s[0]), nj = g.wy(cj + s[1]), nk = NDIM == 3 ? g.wz(ck + s[2]) : 0;
-    cell = pack_cell(NDIM, ni, nj, nk);
-#pragma unroll
-    for (int ax = 0; ax < NDIM; ++ax) d[ax] = d1[ax];
+    c = pack_cell(NDIM, ni, nj, nk);
 }
 
-// Deposit the queued piece at ring position qhead + j with shared-memory atomics.
+// Deposit the queued piece at ring position idx with shared-memory atomics.
 template <int NDIM>
-__device__ __forceinline__ void drain_one(const QueueSink<NDIM> &qs, const TileCtx &tc, int j, float sgn) {
-    const int idx = (qs.qhead + j) & (kQueue - 1);
-    const float d[3] = {qs.q.d[idx], qs.q.d[kQueue + idx], qs.q.d[2 * kQueue + idx]};
-    const float D[3] = {qs.q.D[idx], qs.q.D[kQueue + idx], qs.q.D[2 * kQueue + idx]};
+__device__ __forceinline__ void drain_one(const int *q_base, const float *q_d, const float *q_D, int idx,
+                                          const TileCtx &tc, float sgn) {
+    const float d[3] = {q_d[idx], q_d[kQueue + idx], NDIM == 3 ? q_d[2 * kQueue + idx] : 0.f};
+    const float D[3] = {q_D[idx], q_D[kQueue + idx], q_D[2 * kQueue + idx]};
     SmemSinkFx sd;
     sd.hi = tc.Jhi; sd.lo = tc.Jlo; sd.sx = tc.sx; sd.sxy = tc.sxy; sd.nodes = tc.nodes;
-    sd.base0 = qs.q.base[idx];
-    sd.set_cell(0, 0, 0);
+    sd.base = q_base[idx];
     deposit_segment<NDIM, float>(d, D, sgn, sd);
 }
 
@@ -319,6 +284,8 @@ __device__ __forceinline__ void drain_one(const QueueSink<NDIM> &qs, const TileC
 template <int NDIM, int THREADS>
 __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile) {
     extern __shared__ float4 smem4[];
+    constexpr int WARPS = THREADS / 32;
+    constexpr int NW = words_per_particle<NDIM>();
     const Geom &g = a.g;
     const TileGeom &T = a.t;
     const int tx = tile % T.ntile[0];
@@ -352,82 +319,154 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
         nB[q] = vb;
     }
     for (int q = threadIdx.x; q < 6 * nodes; q += THREADS) Jhi[q] = 0;   // hi and lo limbs
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    __shared__ int work_ctr[4];
+    __shared__ double kin_sh[2][WARPS];
+    if (threadIdx.x < 4) work_ctr[threadIdx.x] = 0;
+    if (lane == 0) { kin_sh[0][warp] = 0.0; kin_sh[1][warp] = 0.0; }
+    // this warp's piece queue and particle stages
+    int *wsm = Jlo + 3 * nodes + warp * warp_smem_words<NDIM>();
+    int *q_base = wsm;
+    float *q_d = reinterpret_cast<float *>(wsm + kQueue);        // [3][kQueue]
+    float *q_D = q_d + 3 * kQueue;                               // [3][kQueue]
+    const uint32_t *stage = reinterpret_cast<const uint32_t *>(wsm + 7 * kQueue);   // [kStages][NW][32]
+    const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage) + 4u * lane;
     __syncthreads();
 
-    double kin0 = 0.0, kin1 = 0.0;
     RegAcc<NDIM> acc;
     acc.q0 = -1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int work_ctr[4];
-    __shared__ int qcount[THREADS / 32];
-    if (threadIdx.x < 4) work_ctr[threadIdx.x] = 0;
-    if (lane == 0) qcount[warp] = 0;
-    QueueSink<NDIM> qs;
-    qs.acc = &acc;
-    qs.q.base = reinterpret_cast<int *>(Jlo + 3 * nodes) + warp * 7 * kQueue;
-    qs.q.d = reinterpret_cast<float *>(qs.q.base + kQueue);
-    qs.q.D = qs.q.d + 3 * kQueue;
-    qs.q.count = &qcount[warp];
-    qs.qhead = 0;
-    qs.sx = tc.sx;
-    qs.sxy = tc.sxy;
-    __syncthreads();
+    int qhead = 0, qcount = 0;   // warp-uniform state of the piece ring
     for (int sp = 0; sp < a.nspecies; ++sp) {
-        const SpeciesMixed P = a.sp[sp];
+        const SpeciesMixed &P = a.sp[sp];
         const float h = a.h[sp], sgn = a.sgn[sp];
-        KahanF k0, k1;
         const int pbeg = a.tile_start[sp][tile], pend = a.tile_start[sp][tile + 1];
         const int nt = pend - pbeg;
         const int nblk = nt >> 10;                       // full 1024-blocks, stored transposed
         const int nitems = nblk + ((nt - (nblk << 10)) + 31) / 32;   // + 32-particle tail chunks
+        // prefetch the particle of iteration j of an item into stage j % kStages (one group per iteration)
+        auto issue = [&](int base, int j, int kn) {
+            const int p = base + (j << 5) + lane;
+            if (j < kn && p < pend) {
+                const uint32_t sa = stage_s + (uint32_t)((j % kStages) * NW * 128);
+                cp_async4(sa, P.cell + p);
+                cp_async4(sa + 128, P.off[0] + p);
+                cp_async4(sa + 256, P.off[1] + p);
+                if (NDIM == 3) cp_async4(sa + 384, P.off[2] + p);
+                cp_async4(sa + (NW - 3) * 128, P.u[0] + p);
+                cp_async4(sa + (NW - 2) * 128, P.u[1] + p);
+                cp_async4(sa + (NW - 1) * 128, P.u[2] + p);
+            }
+            cp_async_commit();
+        };
         // work items are taken by whole warps from a shared counter
         for (;;) {
             int item = 0;
             if (lane == 0) item = atomicAdd(&work_ctr[sp], 1);
-            item = __shfl_sync(0xffffffffu, item, 0);
+            item = __shfl_sync(kFull, item, 0);
             if (item >= nitems) break;
             // block item: lane walks base + 32k + lane, k = 0..31 (consecutive ranks);
             // tail chunk: one element per lane in rank order
             const int base = item < nblk ? pbeg + (item << 10) : pbeg + (nblk << 10) + ((item - nblk) << 5);
             const int kn = item < nblk ? 32 : 1;
+            float kin0 = 0.f, kin1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < kStages - 1; ++j) issue(base, j, kn);
 #pragma unroll 1
             for (int k = 0; k < kn; ++k) {
+                issue(base, k + kStages - 1, kn);
+                cp_async_wait<kStages - 1>();   // this lane's words of iteration k have landed
                 const int p = base + (k << 5) + lane;
+                int nc = 0, q0 = 0;
+                PathSplit<NDIM, float> ps;
                 if (p < pend) {
-                    uint32_t c = P.cell[p];
-                    float d[3] = {P.off[0][p], P.off[1][p], NDIM == 3 ? P.off[2][p] : 0.f};
-                    float u[3] = {P.u[0][p], P.u[1][p], P.u[2][p]};
-                    push_one<NDIM>(a, tc, qs, h, sgn, c, d, u, k0, k1);
+                    const uint32_t *st = stage + (k % kStages) * NW * 32 + lane;
+                    uint32_t c = st[0];
+                    float d[3] = {__uint_as_float(st[32]), __uint_as_float(st[64]),
+                                  NDIM == 3 ? __uint_as_float(st[96]) : 0.f};
+                    float u[3] = {__uint_as_float(st[(NW - 3) * 32]), __uint_as_float(st[(NW - 2) * 32]),
+                                  __uint_as_float(st[(NW - 1) * 32])};
+                    float d0[3], D[3];
+                    int s[3], ci, cj, ck;
+                    bool fast;
+                    push_one<NDIM>(a, tc, h, c, d, u, d0, s, D, fast, q0, ci, cj, ck, kin0, kin1);
                     P.cell[p] = c;
                     P.off[0][p] = d[0];
                     P.off[1][p] = d[1];
                     if (NDIM == 3) P.off[2][p] = d[2];
                     P.u[0][p] = u[0]; P.u[1][p] = u[1]; P.u[2][p] = u[2];
+                    if (fast) {
+                        // the start-cell piece goes to the register accumulator
+                        if (acc.q0 != q0) {
+                            acc.flush(Jhi, Jlo, nodes, tc.sx, tc.sxy);
+                            acc.reset(q0);
+                        }
+                        ps.init(d0, s, d, D[2]);
+                        int cc[3];
+                        float pd[3], pD[3];
+                        ps.piece(0, cc, pd, pD);
+                        deposit_segment<NDIM, float>(pd, pD, sgn, acc);
+                        nc = ps.ncross;
+                    } else {
+                        deposit_global<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, s, d, D[2], sgn);
+                    }
                 }
-                __syncwarp();
-                int waiting = qcount[warp];
-                // deposit waiting pieces 32 at a time, one per lane, all lanes active
-                const bool last = k + 1 == kn;
-                while (waiting >= 32 || (last && waiting > 0)) {
-                    if (lane < waiting) drain_one<NDIM>(qs, tc, lane, sgn);
-                    const int took = waiting < 32 ? waiting : 32;
-                    qs.qhead = (qs.qhead + took) & (kQueue - 1);
-                    waiting -= took;
+                // pieces after a crossing: append to the warp's ring, drain 32 at a time
+                const int kmax = __reduce_max_sync(kFull, nc);
+#pragma unroll 1
+                for (int kp = 1; kp <= kmax; ++kp) {
+                    const bool has = kp <= nc;
+                    const unsigned m = __ballot_sync(kFull, has);
+                    if (has) {
+                        int cc[3];
+                        float pd[3], pD[3];
+                        ps.piece(kp, cc, pd, pD);
+                        const int idx = (qhead + qcount + __popc(m & lt_mask)) & (kQueue - 1);
+                        q_base[idx] = q0 + cc[0] + cc[1] * tc.sx + cc[2] * tc.sxy;
+                        q_d[idx] = pd[0];
+                        q_d[kQueue + idx] = pd[1];
+                        if (NDIM == 3) q_d[2 * kQueue + idx] = pd[2];
+                        q_D[idx] = pD[0];
+                        q_D[kQueue + idx] = pD[1];
+                        q_D[2 * kQueue + idx] = pD[2];
+                    }
+                    qcount += __popc(m);
+                    if (qcount >= 32) {
+                        __syncwarp();
+                        drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, sgn);
+                        __syncwarp();
+                        qhead = (qhead + 32) & (kQueue - 1);
+                        qcount -= 32;
+                    }
                 }
-                __syncwarp();
-                if (lane == 0) qcount[warp] = waiting;
-                __syncwarp();
             }
-            acc.flush(Jhi, Jlo, nodes, tc.sx, tc.sxy);
+            // kinetic energy of the item (at most 32 values per lane in FP32), summed per warp in FP64
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                kin0 += __shfl_xor_sync(kFull, kin0, o);
+                kin1 += __shfl_xor_sync(kFull, kin1, o);
+            }
+            if (lane == 0) {
+                kin_sh[0][warp] += a.m_over_me[sp] * (double)kin0;
+                kin_sh[1][warp] += a.m_over_me[sp] * (double)kin1;
+            }
         }
-        kin0 += a.m_over_me[sp] * ((double)k0.s - (double)k0.c);
-        kin1 += a.m_over_me[sp] * ((double)k1.s - (double)k1.c);
+        // the queued pieces carry this species' sign: deposit them before the next species
+        if (qcount > 0) {
+            __syncwarp();
+            if (lane < qcount) drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, sgn);
+            __syncwarp();
+            qhead = (qhead + qcount) & (kQueue - 1);
+            qcount = 0;
+        }
     }
+    acc.flush(Jhi, Jlo, nodes, tc.sx, tc.sxy);
     __syncthreads();
 
     // Flush the tile current into the padded global int64 current.
     for (int q = threadIdx.x; q < 3 * nodes; q += THREADS) {
-        const long long v = (long long)Jhi[q] * 262144LL + (long long)Jlo[q];
+        const long long v = (long long)Jhi[q] * 262144LL + (long long)Jlo[q] * 1024LL;
         if (v == 0) continue;
         const int comp = q / nodes, r = q - comp * nodes;
         const int lx = r % tc.Rx, ly = (r / tc.Rx) % tc.Ry, lz = r / tc.sxy;
@@ -435,15 +474,10 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
         if (gx < g.px && gy < g.py && gz < g.pz)
             atomicAdd(a.J[comp] + ((long long)gz * g.py + gy) * g.px + gx, (unsigned long long)v);
     }
-    if (a.kin_acc) {
-        for (int o = 16; o > 0; o >>= 1) {
-            kin0 += __shfl_xor_sync(0xffffffffu, kin0, o);
-            kin1 += __shfl_xor_sync(0xffffffffu, kin1, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(a.kin_acc, kin0);
-            atomicAdd(a.kin_acc + 1, kin1);
-        }
+    if (a.kin_acc && threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < WARPS; ++w) t += kin_sh[threadIdx.x][w];
+        atomicAdd(a.kin_acc + threadIdx.x, t);
     }
     __syncthreads();   // shared memory is reused by the next tile of a persistent CTA
 }
@@ -510,7 +544,8 @@ void launch_t(const MixedStepArgs &a, size_t smem, cudaStream_t s) {
 size_t mixed_smem_bytes(const TileGeom &t, int ndim) {
     const size_t nodes = (size_t)t.R[0] * t.R[1] * (ndim == 3 ? t.R[2] : 1);
     const int warps = (ndim == 3 ? 512 : 256) / 32;
-    return nodes * (sizeof(float4) + sizeof(float2) + 6 * sizeof(int)) + (size_t)warps * 7 * kQueue * sizeof(int);
+    const size_t wwords = ndim == 3 ? warp_smem_words<3>() : warp_smem_words<2>();
+    return nodes * (sizeof(float4) + sizeof(float2) + 6 * sizeof(int)) + (size_t)warps * wwords * sizeof(int);
 }
 
 void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
