@@ -92,6 +92,10 @@ struct pic_ctx {
     int multi_nblocks = 0;
     bool multi_tiles_dirty = false;
     std::vector<MixedStepArgs> h_args;
+    SortArgs *sort_args_dev = nullptr;    // one species of every run, for the batched sort
+    int *sort_prefix_dev = nullptr;       // 4 x (nruns + 1) block prefixes of its phases
+    std::vector<SortArgs> h_sort;
+    std::vector<int> h_sort_prefix;
     std::vector<FieldRunF> h_fe, h_fp;
     // PIC_FLAG_TIMING: event pairs per kernel class, resolved in pic_kernel_time
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[3];
@@ -380,7 +384,12 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     const bool mixed = ctx->precision == PIC_MIXED;
     int max_tiles = 1;
     long long max_keys = 1;
-    if (mixed) choose_tiles(r, o, max_tiles, max_keys);
+    if (mixed) {
+        choose_tiles(r, o, max_tiles, max_keys);
+        if (mixed_smem_bytes(r.t, d.ndim) > kMaxPushSmem)
+            return fail(ctx, PIC_EINVAL, "tile %dx%dx%d needs more shared memory than a CTA has", r.t.T[0], r.t.T[1],
+                        r.t.T[2]);
+    }
     const int G = mixed ? r.t.H : 0;
     Geom &g = r.g;
     g.ndim = d.ndim; g.nx = d.nx; g.ny = d.ny; g.nz = d.ndim == 2 ? 1 : d.nz;
@@ -477,7 +486,7 @@ pic_status read_err(pic_ctx *ctx) {
 
 // ------------------------------------------------------------ stepping
 
-void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
+SortArgs sort_args(pic_ctx *ctx, Run &r, SpeciesState &S) {
     SortArgs a;
     a.g = r.g;
     a.t = r.t;
@@ -492,11 +501,20 @@ void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
     a.tile_start = S.tile_start_alt;
     a.perm = r.perm;
     a.err = ctx->d_err;
-    launch_sort(a, ctx->stream);
+    return a;
+}
+
+// Host bookkeeping after the sort of S was enqueued: the sorted copy becomes current.
+void sort_done(Run &r, SpeciesState &S) {
     S.cur = 1 - S.cur;
     std::swap(S.tile_start, S.tile_start_alt);
     S.tiled = true;
     S.tiled_ntiles = r.t.ntiles;
+}
+
+void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
+    launch_sort(sort_args(ctx, r, S), ctx->stream);
+    sort_done(r, S);
 }
 
 MixedStepArgs mixed_args(pic_ctx *ctx, Run &r, double *hslot) {
@@ -545,13 +563,40 @@ pic_status step_multi(pic_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     const int nr = (int)ctx->runs.size();
     int launches = 0;
-    for (auto &r : ctx->runs) {
+    // runs whose sort is due: species q of all of them is sorted by one launch per phase
+    std::vector<int> due;
+    int maxsp = 0;
+    for (int i = 0; i < nr; ++i) {
+        Run &r = ctx->runs[i];
         if (!r.sorted || r.since_sort >= r.sort_interval) {
-            KTimer t(ctx, PIC_KERNEL_SORT);
-            for (int q = 0; q < r.d.nspecies; ++q) sort_species(ctx, r, r.sp[q]);
-            r.sorted = true;
-            r.since_sort = 0;
-            launches += 7 * r.d.nspecies;
+            due.push_back(i);
+            maxsp = std::max(maxsp, r.d.nspecies);
+        }
+    }
+    if (!due.empty()) {
+        KTimer t(ctx, PIC_KERNEL_SORT);
+        for (int q = 0; q < maxsp; ++q) {
+            int ns = 0;
+            for (int i : due) {
+                Run &r = ctx->runs[i];
+                if (q < r.d.nspecies) ctx->h_sort[ns++] = sort_args(ctx, r, r.sp[q]);
+            }
+            sort_multi_prefixes(ctx->h_sort.data(), ns, ctx->h_sort_prefix.data());
+            CK(cudaMemcpyAsync(ctx->sort_args_dev, ctx->h_sort.data(), sizeof(SortArgs) * ns, cudaMemcpyHostToDevice,
+                               s));
+            CK(cudaMemcpyAsync(ctx->sort_prefix_dev, ctx->h_sort_prefix.data(), sizeof(int) * 4 * (ns + 1),
+                               cudaMemcpyHostToDevice, s));
+            launch_sort_multi(ctx->sort_args_dev, ctx->sort_prefix_dev, ctx->h_sort_prefix.data(), ns,
+                              ctx->runs[0].d.ndim, s);
+            for (int i : due) {
+                Run &r = ctx->runs[i];
+                if (q < r.d.nspecies) sort_done(r, r.sp[q]);
+            }
+            launches += 7;
+        }
+        for (int i : due) {
+            ctx->runs[i].sorted = true;
+            ctx->runs[i].since_sort = 0;
         }
     }
     if (ctx->multi_tiles_dirty) {
@@ -746,8 +791,12 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
         ctx->multi_tiles = (int *)dev_alloc(ctx, sizeof(int) * (nruns + 1));
         ctx->multi_blocks = (int *)dev_alloc(ctx, sizeof(int) * (nruns + 1));
         ctx->multi_counter = (int *)dev_alloc(ctx, sizeof(int));
+        ctx->sort_args_dev = (SortArgs *)dev_alloc(ctx, sizeof(SortArgs) * nruns);
+        ctx->sort_prefix_dev = (int *)dev_alloc(ctx, sizeof(int) * 4 * (nruns + 1));
+        ctx->h_sort.resize(nruns);
+        ctx->h_sort_prefix.resize(4 * (nruns + 1));
         if (!ctx->multi_args || !ctx->multi_fe || !ctx->multi_fp || !ctx->multi_tiles || !ctx->multi_blocks ||
-            !ctx->multi_counter) {
+            !ctx->multi_counter || !ctx->sort_args_dev || !ctx->sort_prefix_dev) {
             pic_destroy(ctx);
             return PIC_ENOMEM;
         }
@@ -1151,7 +1200,7 @@ pic_status pic_autotune(pic_ctx *ctx, int max_steps, int tile[3], int *sort_inte
                     for (auto &r : ctx->runs) {
                         const TileGeom t = make_tile_geom(r.d, T, r.t.H);
                         if (t.ntiles > r.max_tiles) fits = false;
-                        if (mixed_smem_bytes(t, ndim) > 220 * 1024) fits = false;
+                        if (mixed_smem_bytes(t, ndim) > kMaxPushSmem) fits = false;
                     }
                     if (!fits) continue;
                     apply_tuning(ctx, T, K);

@@ -145,6 +145,8 @@ void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_
 void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
                             float h, float dt, cudaStream_t s);
 size_t mixed_smem_bytes(const TileGeom &t, int ndim);
+// dynamic shared memory a push CTA may use (227 KB per block, less the kernels' static shared memory)
+constexpr size_t kMaxPushSmem = 224 * 1024;
 
 // sort.cu
 struct SortArgs {
@@ -161,6 +163,12 @@ struct SortArgs {
     int *err;
 };
 void launch_sort(const SortArgs &a, cudaStream_t s);
+// many independent sorts in one launch per phase: h_prefix (4 x (nsort + 1) ints)
+// is filled by sort_multi_prefixes from the host copy of the arguments and
+// uploaded to d_prefix next to d_args
+void sort_multi_prefixes(const SortArgs *h_args, int nsort, int *h_prefix);
+void launch_sort_multi(const SortArgs *d_args, const int *d_prefix, const int *h_prefix, int nsort, int ndim,
+                       cudaStream_t s);
 size_t sort_scan_scratch(long long nkeys);
 
 // mj.cu

@@ -195,11 +195,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 constexpr int kQueue = 64;      // per-warp ring of waiting pieces (at most 63 wait at any time)
 constexpr int kStages = 3;      // per-warp particle prefetch ring
-template <int NDIM> __host__ __device__ constexpr int words_per_particle() { return NDIM == 3 ? 7 : 6; }
+// words of one particle in a stage: cell, NDIM offsets, 3 momenta
+template <int NDIM> __host__ __device__ constexpr int words_per_particle() { return NDIM + 4; }
 
 // Shared memory of one warp after the node fields and the current limbs: the
 // piece queue (cell base, d[3], D[3]: 7 x kQueue words) and the particle
-// stages (kStages x words_per_particle x 32 words).
+// stages (kStages x words_per_particle x 32 words, word-major).
 template <int NDIM>
 __host__ __device__ constexpr int warp_smem_words() { return 7 * kQueue + kStages * words_per_particle<NDIM>() * 32; }
 
@@ -354,9 +355,9 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                 cp_async4(sa + 128, P.off[0] + p);
                 cp_async4(sa + 256, P.off[1] + p);
                 if (NDIM == 3) cp_async4(sa + 384, P.off[2] + p);
-                cp_async4(sa + (NW - 3) * 128, P.u[0] + p);
-                cp_async4(sa + (NW - 2) * 128, P.u[1] + p);
-                cp_async4(sa + (NW - 1) * 128, P.u[2] + p);
+                cp_async4(sa + (NDIM + 1) * 128, P.u[0] + p);
+                cp_async4(sa + (NDIM + 2) * 128, P.u[1] + p);
+                cp_async4(sa + (NDIM + 3) * 128, P.u[2] + p);
             }
             cp_async_commit();
         };
@@ -385,8 +386,8 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                     uint32_t c = st[0];
                     float d[3] = {__uint_as_float(st[32]), __uint_as_float(st[64]),
                                   NDIM == 3 ? __uint_as_float(st[96]) : 0.f};
-                    float u[3] = {__uint_as_float(st[(NW - 3) * 32]), __uint_as_float(st[(NW - 2) * 32]),
-                                  __uint_as_float(st[(NW - 1) * 32])};
+                    float u[3] = {__uint_as_float(st[(NDIM + 1) * 32]), __uint_as_float(st[(NDIM + 2) * 32]),
+                                  __uint_as_float(st[(NDIM + 3) * 32])};
                     float d0[3], D[3];
                     int s[3], ci, cj, ck;
                     bool fast;

@@ -13,7 +13,8 @@
 // read from the scanned counts.
 //
 // Roofline: HBM bound; per particle 4 B (histogram) + 8 B (rank) +
-// 4 + 2 x (24..28 + 4) B (gather) plus per key 3 x 4 B.
+// 4 + 2 x (24..28 + 4) B (gather) plus per key 3 x 4 B.  Particle counts are
+// int32 (at most 2^31 - 1 particles per species).
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -53,47 +54,48 @@ __device__ __forceinline__ int interleaved_slot(int r, int n_t) {
 struct SrcWalk {
     const int *old_start;   // old tile offsets, or nullptr when the source is untiled
     long long n;
-    __device__ __forceinline__ bool begin(long long &i, long long &end, int &t0, int &nt) const {
+    int b, nb;              // this block and the block count of the walk
+    __device__ __forceinline__ void begin(long long &i, long long &end, int &t0, int &nt) const {
         if (old_start) {
-            t0 = old_start[blockIdx.x];
-            nt = old_start[blockIdx.x + 1] - t0;
+            t0 = old_start[b];
+            nt = old_start[b + 1] - t0;
             i = threadIdx.x;
             end = nt;
         } else {
             t0 = 0;
             nt = 0;
-            i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+            i = (long long)b * blockDim.x + threadIdx.x;
             end = n;
         }
-        return true;
     }
     __device__ __forceinline__ long long step() const {
-        return old_start ? (long long)blockDim.x : (long long)gridDim.x * blockDim.x;
+        return old_start ? (long long)blockDim.x : (long long)nb * blockDim.x;
     }
     __device__ __forceinline__ long long pos(long long i, int t0, int nt) const {
         return old_start ? (long long)t0 + interleaved_slot((int)i, nt) : i;
     }
 };
 
-__global__ void k_zero(int *a, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        a[i] = 0;
+// ---- phase bodies, written for block b of nb blocks working on one sort ----
+
+__device__ inline void zero_body(int *a, long long n, int b, int nb) {
+    for (long long i = (long long)b * blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) a[i] = 0;
 }
 
 template <int NDIM>
-__global__ void k_histogram(TileGeom t, const uint32_t *cell, SrcWalk w, int *counts, long long nkeys, int *err) {
+__device__ inline void histogram_body(const SortArgs &a, const SrcWalk &w, long long nkeys) {
     long long i, end;
     int t0, nt;
     w.begin(i, end, t0, nt);
     for (; i < end; i += w.step()) {
         const long long p = w.pos(i, t0, nt);
-        const int key = cell_key<NDIM>(t, cell[p]);
-        if (key < 0 || key >= nkeys) { atomicOr(err, ERR_SORT); continue; }
+        const int key = cell_key<NDIM>(a.t, a.src.cell[p]);
+        if (key < 0 || key >= nkeys) { atomicOr(a.err, ERR_SORT); continue; }
         // warp aggregation: lanes with the same key add once
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, key);
         const int leader = __ffs(peers) - 1;
-        if ((int)(threadIdx.x & 31) == leader) atomicAdd(counts + key, __popc(peers));
+        if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + key, __popc(peers));
     }
 }
 
@@ -129,9 +131,9 @@ __device__ inline int block_scan(int (&v)[kScanItems], int *sh) {
     return total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const int *in, int *out, int *block_sums, long long n) {
-    __shared__ int sh[33];
-    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+// Scan of block b's kScanTile counts into offsets; the block total goes to block_sums[b].
+__device__ inline void scan_blocks_body(const int *in, int *out, int *block_sums, long long n, int b, int *sh) {
+    const long long base = (long long)b * kScanTile + (long long)threadIdx.x * kScanItems;
     int v[kScanItems];
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) v[q] = base + q < n ? in[base + q] : 0;
@@ -139,12 +141,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const int *in, int
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q)
         if (base + q < n) out[base + q] = v[q];
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+    if (threadIdx.x == 0) block_sums[b] = total;
 }
 
 // Exclusive scan of the block sums in one block (any count, in chunks).
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *block_sums, int nb) {
-    __shared__ int sh[33];
+__device__ inline void scan_sums_body(int *block_sums, int nb, int *sh) {
     int carry = 0;
     for (int base = 0; base < nb; base += kScanTile) {
         int v[kScanItems];
@@ -159,65 +160,194 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *block_sums, int
     }
 }
 
-// Add block offsets; copy to cursors; extract tile offsets.
-__global__ void k_scan_finish(int *offsets, int *cursors, const int *block_sums, long long nkeys, int cells_per_tile,
-                              int ntiles, int *tile_start, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nkeys;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int v = offsets[i] + block_sums[i / kScanTile];
-        offsets[i] = v;
-        cursors[i] = v;
-        if (i % cells_per_tile == 0) tile_start[i / cells_per_tile] = v;
+// Add block offsets; copy to the cursors (counts array); extract tile offsets.
+__device__ inline void scan_finish_body(const SortArgs &a, long long nkeys, int b, int nb) {
+    for (long long i = (long long)b * blockDim.x + threadIdx.x; i < nkeys; i += (long long)nb * blockDim.x) {
+        const int v = a.offsets[i] + a.block_sums[i / kScanTile];
+        a.offsets[i] = v;
+        a.counts[i] = v;
+        if (i % a.t.cells_per_tile == 0) a.tile_start[i / a.t.cells_per_tile] = v;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) tile_start[ntiles] = (int)n;
+    if (b == 0 && threadIdx.x == 0) a.tile_start[a.t.ntiles] = (int)a.n;
 }
 
 // Rank pass: the destination slot of every source particle, written as the
 // inverse permutation perm[slot] = source index (4-byte scattered writes only).
 template <int NDIM>
-__global__ void k_rank(TileGeom t, const uint32_t *cell, SrcWalk w, int *cursors, long long nkeys,
-                       const int *tile_start, int *perm) {
+__device__ inline void rank_body(const SortArgs &a, const SrcWalk &w, long long nkeys) {
     long long i, end;
     int t0s, nts;
     w.begin(i, end, t0s, nts);
     for (; i < end; i += w.step()) {
         const long long p = w.pos(i, t0s, nts);
-        const int key = cell_key<NDIM>(t, cell[p]);
+        const int key = cell_key<NDIM>(a.t, a.src.cell[p]);
         if (key < 0 || key >= nkeys) continue;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, key);
         const int lane = threadIdx.x & 31;
         const int leader = __ffs(peers) - 1;
         int base = 0;
-        if (lane == leader) base = atomicAdd(cursors + key, __popc(peers));
+        if (lane == leader) base = atomicAdd(a.counts + key, __popc(peers));
         base = __shfl_sync(peers, base, leader);
         const int rank = base + __popc(peers & ((1u << lane) - 1u));
-        const int tile = key / t.cells_per_tile;
-        const int t0 = tile_start[tile], t1 = tile_start[tile + 1];
-        perm[t0 + interleaved_slot(rank - t0, t1 - t0)] = (int)p;
+        const int tile = key / a.t.cells_per_tile;
+        const int t0 = a.tile_start[tile], t1 = a.tile_start[tile + 1];
+        a.perm[t0 + interleaved_slot(rank - t0, t1 - t0)] = (int)p;
     }
 }
 
-// Gather pass in destination order: coalesced writes, reads through L2.
+// Gather pass in destination order.  One CTA per chunk of kGatherChunk
+// destination slots, one particle array at a time: the sources of a chunk lie
+// in the same tile of the previous layout (plus the few particles that changed
+// tile), so while the resident CTAs work on one array the source regions they
+// read stay in L2 and every source sector comes from DRAM about once.  (A
+// grid-stride loop over the whole array spreads the resident threads over all
+// of it and fetches each 32-byte sector many times for its 4 used bytes.)
+constexpr int kGatherThreads = 256;
+constexpr int kGatherChunk = 8192;
+
 template <int NDIM>
-__global__ void k_gather(SpeciesMixed src, SpeciesMixed dst, long long n, const int *perm) {
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const int p = perm[q];
-        dst.cell[q] = __ldg(src.cell + p);
-        dst.off[0][q] = __ldg(src.off[0] + p);
-        dst.off[1][q] = __ldg(src.off[1] + p);
-        if (NDIM == 3) dst.off[2][q] = __ldg(src.off[2] + p);
-        dst.u[0][q] = __ldg(src.u[0] + p);
-        dst.u[1][q] = __ldg(src.u[1] + p);
-        dst.u[2][q] = __ldg(src.u[2] + p);
-        dst.id[q] = __ldg(src.id + p);
+__device__ inline void gather_body(const SpeciesMixed &src, const SpeciesMixed &dst, long long n, const int *perm,
+                                   int b) {
+    constexpr int NA = NDIM + 5;   // cell, offsets, 3 momenta, id
+    const long long q0 = (long long)b * kGatherChunk;
+    const long long q1 = q0 + kGatherChunk < n ? q0 + kGatherChunk : n;
+#pragma unroll 1
+    for (int a = 0; a < NA; ++a) {
+        const uint32_t *sa;
+        uint32_t *da;
+        if (a == 0) { sa = src.cell; da = dst.cell; }
+        else if (a <= NDIM) { sa = reinterpret_cast<const uint32_t *>(src.off[a - 1]);
+                              da = reinterpret_cast<uint32_t *>(dst.off[a - 1]); }
+        else if (a < NA - 1) { sa = reinterpret_cast<const uint32_t *>(src.u[a - 1 - NDIM]);
+                               da = reinterpret_cast<uint32_t *>(dst.u[a - 1 - NDIM]); }
+        else { sa = reinterpret_cast<const uint32_t *>(src.id); da = reinterpret_cast<uint32_t *>(dst.id); }
+        // four independent loads in flight per thread
+        for (long long q = q0 + threadIdx.x; q < q1; q += 4 * kGatherThreads) {
+            int p[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const long long qq = q + v * kGatherThreads;
+                p[v] = qq < q1 ? __ldg(perm + qq) : -1;
+            }
+            uint32_t x[4];
+            // an out-of-range entry exists only after a bad key, which the histogram has flagged
+#pragma unroll
+            for (int v = 0; v < 4; ++v) x[v] = (p[v] >= 0 && p[v] < n) ? __ldg(sa + p[v]) : 0u;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const long long qq = q + v * kGatherThreads;
+                if (qq < q1) da[qq] = x[v];
+            }
+        }
     }
 }
+
+// ---- block counts of the phases of one sort ----
 
 inline int blocks_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     const long long cap = 152LL * 32;
     return (int)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+__host__ __device__ inline long long nkeys_of(const SortArgs &a) { return (long long)a.t.ntiles * a.t.cells_per_tile; }
+inline int walk_blocks(const SortArgs &a) { return a.old_tile_start ? a.t.ntiles : blocks_for(a.n, 256); }
+__host__ __device__ inline int scan_blocks(const SortArgs &a) { return (int)((nkeys_of(a) + kScanTile - 1) / kScanTile); }
+inline int key_blocks(const SortArgs &a) { return blocks_for(nkeys_of(a), 256); }
+inline int gather_blocks(const SortArgs &a) { return (int)((a.n + kGatherChunk - 1) / kGatherChunk); }
+
+// ---- one sort: one launch per phase ----
+
+__global__ void k_zero(SortArgs a) { zero_body(a.counts, nkeys_of(a), blockIdx.x, gridDim.x); }
+
+template <int NDIM>
+__global__ void k_histogram(SortArgs a) {
+    const SrcWalk w{a.old_tile_start, a.n, (int)blockIdx.x, (int)gridDim.x};
+    histogram_body<NDIM>(a, w, nkeys_of(a));
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(SortArgs a) {
+    __shared__ int sh[33];
+    scan_blocks_body(a.counts, a.offsets, a.block_sums, nkeys_of(a), blockIdx.x, sh);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(SortArgs a) {
+    __shared__ int sh[33];
+    scan_sums_body(a.block_sums, scan_blocks(a), sh);
+}
+
+__global__ void k_scan_finish(SortArgs a) { scan_finish_body(a, nkeys_of(a), blockIdx.x, gridDim.x); }
+
+template <int NDIM>
+__global__ void k_rank(SortArgs a) {
+    const SrcWalk w{a.old_tile_start, a.n, (int)blockIdx.x, (int)gridDim.x};
+    rank_body<NDIM>(a, w, nkeys_of(a));
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(SortArgs a) {
+    gather_body<NDIM>(a.src, a.dst, a.n, a.perm, blockIdx.x);
+}
+
+// ---- many independent sorts (one species of every run of an ensemble): one
+// launch per phase; block B belongs to sort s with prefix[s] <= B < prefix[s+1]
+// of that phase's block prefix. ----
+
+__device__ inline int find_sort(const int *prefix, int nsort, int B) {
+    int lo = 0, hi = nsort;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= B) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_zero_multi(const SortArgs *as, const int *prefix, int nsort) {
+    const int s = find_sort(prefix, nsort, blockIdx.x);
+    const SortArgs &a = as[s];
+    zero_body(a.counts, nkeys_of(a), blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]);
+}
+
+template <int NDIM>
+__global__ void k_histogram_multi(const SortArgs *as, const int *prefix, int nsort) {
+    const int s = find_sort(prefix, nsort, blockIdx.x);
+    const SortArgs &a = as[s];
+    const SrcWalk w{a.old_tile_start, a.n, (int)blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]};
+    histogram_body<NDIM>(a, w, nkeys_of(a));
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks_multi(const SortArgs *as, const int *prefix,
+                                                                    int nsort) {
+    __shared__ int sh[33];
+    const int s = find_sort(prefix, nsort, blockIdx.x);
+    const SortArgs &a = as[s];
+    scan_blocks_body(a.counts, a.offsets, a.block_sums, nkeys_of(a), blockIdx.x - prefix[s], sh);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums_multi(const SortArgs *as) {
+    __shared__ int sh[33];
+    const SortArgs &a = as[blockIdx.x];
+    scan_sums_body(a.block_sums, scan_blocks(a), sh);
+}
+
+__global__ void k_scan_finish_multi(const SortArgs *as, const int *prefix, int nsort) {
+    const int s = find_sort(prefix, nsort, blockIdx.x);
+    scan_finish_body(as[s], nkeys_of(as[s]), blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]);
+}
+
+template <int NDIM>
+__global__ void k_rank_multi(const SortArgs *as, const int *prefix, int nsort) {
+    const int s = find_sort(prefix, nsort, blockIdx.x);
+    const SortArgs &a = as[s];
+    const SrcWalk w{a.old_tile_start, a.n, (int)blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]};
+    rank_body<NDIM>(a, w, nkeys_of(a));
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kGatherThreads) k_gather_multi(const SortArgs *as, const int *prefix, int nsort) {
+    const int s = find_sort(prefix, nsort, blockIdx.x);
+    const SortArgs &a = as[s];
+    gather_body<NDIM>(a.src, a.dst, a.n, a.perm, blockIdx.x - prefix[s]);
 }
 
 }  // namespace
@@ -225,29 +355,60 @@ inline int blocks_for(long long n, int threads) {
 size_t sort_scan_scratch(long long nkeys) { return (size_t)((nkeys + kScanTile - 1) / kScanTile + 1); }
 
 void launch_sort(const SortArgs &a, cudaStream_t s) {
-    const long long nkeys = (long long)a.t.ntiles * a.t.cells_per_tile;
-    SrcWalk w;
-    w.old_start = a.old_tile_start;
-    w.n = a.n;
-    const int wblocks = a.old_tile_start ? a.t.ntiles : blocks_for(a.n, 256);
-    k_zero<<<blocks_for(nkeys, 256), 256, 0, s>>>(a.counts, nkeys);
+    k_zero<<<key_blocks(a), 256, 0, s>>>(a);
     if (a.n > 0) {
-        if (a.g.ndim == 3) k_histogram<3><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.err);
-        else k_histogram<2><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.err);
+        if (a.g.ndim == 3) k_histogram<3><<<walk_blocks(a), 256, 0, s>>>(a);
+        else k_histogram<2><<<walk_blocks(a), 256, 0, s>>>(a);
     }
-    const int nb = (int)((nkeys + kScanTile - 1) / kScanTile);
-    k_scan_blocks<<<nb, kScanThreads, 0, s>>>(a.counts, a.offsets, a.block_sums, nkeys);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
-    k_scan_finish<<<blocks_for(nkeys, 256), 256, 0, s>>>(a.offsets, a.counts, a.block_sums, nkeys,
-                                                         a.t.cells_per_tile, a.t.ntiles, a.tile_start, a.n);
+    k_scan_blocks<<<scan_blocks(a), kScanThreads, 0, s>>>(a);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(a);
+    k_scan_finish<<<key_blocks(a), 256, 0, s>>>(a);
     if (a.n > 0) {
         if (a.g.ndim == 3) {
-            k_rank<3><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.tile_start, a.perm);
-            k_gather<3><<<blocks_for(a.n, 256), 256, 0, s>>>(a.src, a.dst, a.n, a.perm);
+            k_rank<3><<<walk_blocks(a), 256, 0, s>>>(a);
+            k_gather<3><<<gather_blocks(a), kGatherThreads, 0, s>>>(a);
         } else {
-            k_rank<2><<<wblocks, 256, 0, s>>>(a.t, a.src.cell, w, a.counts, nkeys, a.tile_start, a.perm);
-            k_gather<2><<<blocks_for(a.n, 256), 256, 0, s>>>(a.src, a.dst, a.n, a.perm);
+            k_rank<2><<<walk_blocks(a), 256, 0, s>>>(a);
+            k_gather<2><<<gather_blocks(a), kGatherThreads, 0, s>>>(a);
         }
+    }
+}
+
+void sort_multi_prefixes(const SortArgs *h_args, int nsort, int *h_prefix) {
+    int *pz = h_prefix, *pw = h_prefix + (nsort + 1), *pb = h_prefix + 2 * (nsort + 1),
+        *pg = h_prefix + 3 * (nsort + 1);
+    pz[0] = pw[0] = pb[0] = pg[0] = 0;
+    for (int i = 0; i < nsort; ++i) {
+        const SortArgs &a = h_args[i];
+        pz[i + 1] = pz[i] + key_blocks(a);
+        pw[i + 1] = pw[i] + (a.n > 0 ? walk_blocks(a) : 0);
+        pb[i + 1] = pb[i] + scan_blocks(a);
+        pg[i + 1] = pg[i] + gather_blocks(a);
+    }
+}
+
+void launch_sort_multi(const SortArgs *d_args, const int *d_prefix, const int *h_prefix, int nsort, int ndim,
+                       cudaStream_t s) {
+    if (nsort <= 0) return;
+    const int *pz = d_prefix, *pw = d_prefix + (nsort + 1), *pb = d_prefix + 2 * (nsort + 1),
+              *pg = d_prefix + 3 * (nsort + 1);
+    const int nz = h_prefix[nsort], nw = h_prefix[2 * (nsort + 1) - 1], nb = h_prefix[3 * (nsort + 1) - 1],
+              ng = h_prefix[4 * (nsort + 1) - 1];
+    k_zero_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort);
+    if (nw > 0) {
+        if (ndim == 3) k_histogram_multi<3><<<nw, 256, 0, s>>>(d_args, pw, nsort);
+        else k_histogram_multi<2><<<nw, 256, 0, s>>>(d_args, pw, nsort);
+    }
+    k_scan_blocks_multi<<<nb, kScanThreads, 0, s>>>(d_args, pb, nsort);
+    k_scan_sums_multi<<<nsort, kScanThreads, 0, s>>>(d_args);
+    k_scan_finish_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort);
+    if (nw > 0) {
+        if (ndim == 3) k_rank_multi<3><<<nw, 256, 0, s>>>(d_args, pw, nsort);
+        else k_rank_multi<2><<<nw, 256, 0, s>>>(d_args, pw, nsort);
+    }
+    if (ng > 0) {
+        if (ndim == 3) k_gather_multi<3><<<ng, kGatherThreads, 0, s>>>(d_args, pg, nsort);
+        else k_gather_multi<2><<<ng, kGatherThreads, 0, s>>>(d_args, pg, nsort);
     }
 }
 
