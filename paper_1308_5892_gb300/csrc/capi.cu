@@ -324,10 +324,6 @@ bool validate(const pic_run_desc &d, int precision, std::string &why) {
         if (d.bc[a] != PIC_BC_PERIODIC && d.bc[a] != PIC_BC_CONDUCTOR) { why = "unknown boundary kind"; return false; }
         if (a > 0 && d.bc[a] != PIC_BC_PERIODIC) { why = "conducting walls are supported along x only"; return false; }
     }
-    if (d.bc[0] == PIC_BC_CONDUCTOR && precision == PIC_MIXED) {
-        why = "conducting walls are available in the FP64 path only";
-        return false;
-    }
     return true;
 }
 
@@ -626,7 +622,7 @@ pic_status step_multi(pic_ctx *ctx) {
         KTimer t(ctx, PIC_KERNEL_PUSH);
         CK(cudaMemsetAsync(ctx->multi_counter, 0, sizeof(int), s));
         launch_push_mixed_multi(ctx->multi_args, ctx->multi_tiles, nr, ctx->runs[0].d.ndim, ctx->runs[0].t,
-                                ctx->multi_counter, s);
+                                ctx->runs[0].g.bcx == 1, ctx->multi_counter, s);
     }
     {
         KTimer t(ctx, PIC_KERNEL_FIELD);
@@ -779,7 +775,7 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
         for (int r = 1; r < nruns; ++r) {
             const Run &rr = ctx->runs[r];
             if (rr.d.ndim != r0.d.ndim || rr.t.H != r0.t.H || rr.t.T[0] != r0.t.T[0] || rr.t.T[1] != r0.t.T[1] ||
-                rr.t.T[2] != r0.t.T[2] || rr.sort_interval != r0.sort_interval) {
+                rr.t.T[2] != r0.t.T[2] || rr.sort_interval != r0.sort_interval || rr.g.bcx != r0.g.bcx) {
                 pic_destroy(ctx);
                 return PIC_EINVAL;
             }

@@ -126,7 +126,7 @@ struct MixedStepArgs {
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
 // persistent launch over the tiles of many runs (same ndim and tile shape)
 void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
-                             const TileGeom &t, int *counter, cudaStream_t s);
+                             const TileGeom &t, bool walls, int *counter, cudaStream_t s);
 
 // fields.cu, batched over runs: one launch updates every run's grid
 struct FieldRunF {

@@ -78,6 +78,42 @@ __device__ __noinline__ void deposit_global(const Geom &g, unsigned long long *J
     deposit_path<NDIM, float>(d, s, d1, dz, sgn, pd);
 }
 
+// Slow path of a particle reflected by a conducting wall in x (App. A.4):
+// the path to the wall and the mirrored remainder are deposited as two legs.
+// side -1: wall at the low face of cell ci (x = 0), +1: at its high face (x = nx).
+template <int NDIM>
+__device__ __noinline__ void deposit_reflect(const Geom &g, unsigned long long *J0, unsigned long long *J1,
+                                             unsigned long long *J2, int ci, int cj, int ck, const float d0[3],
+                                             const float D[3], int side, float sgn) {
+    const float wall = side < 0 ? 0.f : 1.f;           // in the x coordinates of cell ci
+    const float t = (wall - d0[0]) / D[0];             // parameter of the wall hit, in [0, 1]
+    const float L1[3] = {wall - d0[0], D[1] * t, D[2] * t};
+    const float L2[3] = {-(D[0] - L1[0]), D[1] - L1[1], D[2] - L1[2]};
+    int c[3] = {ci, cj, ck};
+    float st[3] = {d0[0], d0[1], d0[2]};
+#pragma unroll 1
+    for (int leg = 0; leg < 2; ++leg) {
+        const float *L = leg == 0 ? L1 : L2;
+        int s[3] = {0, 0, 0};
+        float d1[3] = {0.f, 0.f, 0.f};
+        // x stays in cell ci: the first leg ends on the wall, the second starts there
+        d1[0] = leg == 0 ? wall : fminf(fmaxf(wall + L[0], 0.f), 1.f);
+        for (int a = 1; a < NDIM; ++a) {
+            const float pa = st[a] + L[a];
+            float sa = floorf(pa);
+            float da = pa - sa;
+            if (da >= 1.f) { da = 0.f; sa += 1.f; }
+            sa = fminf(fmaxf(sa, -1.f), 1.f);
+            s[a] = (int)sa;
+            d1[a] = da;
+        }
+        deposit_global<NDIM>(g, J0, J1, J2, c[0], c[1], c[2], st, s, d1, L[2], sgn);
+        // the second leg starts where the first ended
+        st[0] = wall;
+        for (int a = 1; a < NDIM; ++a) { c[a] += s[a]; st[a] = d1[a]; }
+    }
+}
+
 template <int NDIM>
 __device__ __forceinline__ void gather_nodes(const float4 *nA, const float2 *nB, int q0, int sx, int sxy,
                                              const float d[3], float E[3], float B[3]) {
@@ -110,7 +146,10 @@ __device__ __noinline__ void gather_global(const Geom &g, const float4 *nA, cons
             for (int eps = 0; eps < 2; ++eps) {
                 float w = (eps ? d[0] : 1.f - d[0]) * (eta ? d[1] : 1.f - d[1]);
                 if (NDIM == 3) w *= (xi ? d[2] : 1.f - d[2]);
-                const long long q = g.widx(ci + eps, cj + eta, ck + xi);
+                // with walls the x node is not wrapped: node nx lies in the padding and holds the
+                // masked averages of the high wall, which differ from node 0's
+                const long long q = g.bcx == 1 ? g.pidx(ci + eps, g.wy(cj + eta), g.wz(ck + xi))
+                                               : g.widx(ci + eps, cj + eta, ck + xi);
                 const float4 a = __ldg(nA + q);
                 const float2 b = __ldg(nB + q);
                 E[0] += w * a.x; E[1] += w * a.y; E[2] += w * a.z;
@@ -216,10 +255,10 @@ struct TileCtx {
 // state; d0, s, D describe the path for the deposit; fast tells whether the
 // stencil stays in the staged box, and q0 is then the local node index of the
 // start cell.
-template <int NDIM>
+template <int NDIM, bool WALLS>
 __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &tc, float h, uint32_t &c, float d[3],
                                          float u[3], float d0[3], int s[3], float D[3], bool &fast, int &q0,
-                                         int &ci, int &cj, int &ck, float &kin0, float &kin1) {
+                                         int &ci, int &cj, int &ck, float &kin0, float &kin1, int &side) {
     const Geom &g = a.g;
     unpack_cell(NDIM, c, ci, cj, ck);
     // local cell in the staged box, nearest periodic image of the tile
@@ -251,6 +290,12 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
         d0[ax] = d[ax];
         s[ax] = 0;
     }
+    // conducting walls in x (App. A.4): a particle that would cross a wall is reflected
+    side = 0;
+    if (WALLS) {
+        const float px = d[0] + D[0];
+        side = (ci == 0 && px < 0.f) ? -1 : ((ci == g.nx - 1 && px > 1.f) ? 1 : 0);
+    }
 #pragma unroll
     for (int ax = 0; ax < NDIM; ++ax) {
         const float pa = d[ax] + D[ax];
@@ -265,7 +310,20 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
         s[ax] = (int)sa;
         d[ax] = da;
     }
-    const int ni = g.wx(ci + s[0]), nj = g.wy(cj + s[1]), nk = NDIM == 3 ? g.wz(ck + s[2]) : 0;
+    if (WALLS && side != 0) {
+        // mirrored end in the same cell, x momentum reversed; deposited by the slow path
+        s[0] = 0;
+        d[0] = fminf(fmaxf(side < 0 ? -(d0[0] + D[0]) : 2.f - (d0[0] + D[0]), 0.f), 1.f);
+        u[0] = -u[0];
+        fast = false;
+    } else if (WALLS && ci + s[0] >= g.nx) {
+        // landed exactly on the high wall: it stays in the last cell at offset 1
+        s[0] = 0;
+        d[0] = 1.f;
+    }
+    // with walls, x is never wrapped (cell 0 and nx - 1 hold the particles at the walls)
+    const int ni = WALLS ? ci + s[0] : g.wx(ci + s[0]);
+    const int nj = g.wy(cj + s[1]), nk = NDIM == 3 ? g.wz(ck + s[2]) : 0;
     c = pack_cell(NDIM, ni, nj, nk);
 }
 
@@ -282,7 +340,7 @@ __device__ __forceinline__ void drain_one(const int *q_base, const float *q_d, c
 }
 
 // All species of one tile of one run (the body of both launch forms below).
-template <int NDIM, int THREADS>
+template <int NDIM, int THREADS, bool WALLS>
 __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile) {
     extern __shared__ float4 smem4[];
     constexpr int WARPS = THREADS / 32;
@@ -389,9 +447,9 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                     float u[3] = {__uint_as_float(st[(NDIM + 1) * 32]), __uint_as_float(st[(NDIM + 2) * 32]),
                                   __uint_as_float(st[(NDIM + 3) * 32])};
                     float d0[3], D[3];
-                    int s[3], ci, cj, ck;
+                    int s[3], ci, cj, ck, side;
                     bool fast;
-                    push_one<NDIM>(a, tc, h, c, d, u, d0, s, D, fast, q0, ci, cj, ck, kin0, kin1);
+                    push_one<NDIM, WALLS>(a, tc, h, c, d, u, d0, s, D, fast, q0, ci, cj, ck, kin0, kin1, side);
                     P.cell[p] = c;
                     P.off[0][p] = d[0];
                     P.off[1][p] = d[1];
@@ -409,8 +467,10 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                         ps.piece(0, cc, pd, pD);
                         deposit_segment<NDIM, float>(pd, pD, sgn, acc);
                         nc = ps.ncross;
-                    } else {
+                    } else if (!WALLS || side == 0) {
                         deposit_global<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, s, d, D[2], sgn);
+                    } else {
+                        deposit_reflect<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, D, side, sgn);
                     }
                 }
                 // pieces after a crossing: append to the warp's ring, drain 32 at a time
@@ -483,17 +543,18 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
     __syncthreads();   // shared memory is reused by the next tile of a persistent CTA
 }
 
-// One CTA per tile of one run.
-template <int NDIM, int THREADS, int MINB>
+// One CTA per tile of one run; WALLS: conducting walls in x (a separate
+// instantiation keeps their register cost out of the periodic kernel).
+template <int NDIM, int THREADS, int MINB, bool WALLS>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(MixedStepArgs a) {
-    push_tile<NDIM, THREADS>(a, blockIdx.x);
+    push_tile<NDIM, THREADS, WALLS>(a, blockIdx.x);
 }
 
 // Persistent form for a batch of independent runs of uneven size: resident
 // CTAs take (run, tile) work items from one counter until all tiles of all
 // runs are done, so small runs do not leave most of the GPU idle.
 // tile_prefix[r] is the number of tiles of runs 0..r-1.
-template <int NDIM, int THREADS, int MINB>
+template <int NDIM, int THREADS, int MINB, bool WALLS>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedStepArgs *runs, const int *tile_prefix,
                                                                     int nruns, int *counter) {
     __shared__ int item_sh;
@@ -513,7 +574,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedS
         int *dst = reinterpret_cast<int *>(&args_sh);
         for (int q = threadIdx.x; q < (int)(sizeof(MixedStepArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
         __syncthreads();
-        push_tile<NDIM, THREADS>(args_sh, item - tile_prefix[lo]);
+        push_tile<NDIM, THREADS, WALLS>(args_sh, item - tile_prefix[lo]);
     }
 }
 
@@ -534,10 +595,11 @@ __global__ void k_half_back_mixed(Geom g, const float4 *nfA, const float2 *nfB, 
     }
 }
 
-template <int NDIM, int THREADS, int MINB>
+template <int NDIM, int THREADS, int MINB, bool WALLS>
 void launch_t(const MixedStepArgs &a, size_t smem, cudaStream_t s) {
-    cudaFuncSetAttribute(k_push_mixed<NDIM, THREADS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_push_mixed<NDIM, THREADS, MINB><<<a.t.ntiles, THREADS, smem, s>>>(a);
+    auto k = k_push_mixed<NDIM, THREADS, MINB, WALLS>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<a.t.ntiles, THREADS, smem, s>>>(a);
 }
 
 }  // namespace
@@ -557,10 +619,10 @@ void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB,
     else k_half_back_mixed<2><<<blocks, 256, 0, s>>>(g, nfA, nfB, sp, n, h, dt);
 }
 
-template <int NDIM, int THREADS, int MINB>
+template <int NDIM, int THREADS, int MINB, bool WALLS>
 void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem,
                     cudaStream_t s) {
-    auto k = k_push_mixed_multi<NDIM, THREADS, MINB>;
+    auto k = k_push_mixed_multi<NDIM, THREADS, MINB, WALLS>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
@@ -571,16 +633,27 @@ void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns
 }
 
 void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
-                             const TileGeom &t, int *counter, cudaStream_t s) {
+                             const TileGeom &t, bool walls, int *counter, cudaStream_t s) {
     const size_t smem = mixed_smem_bytes(t, ndim);
-    if (ndim == 3) launch_multi_t<3, 512, 1>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
-    else launch_multi_t<2, 256, 2>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+    if (ndim == 3) {
+        if (walls) launch_multi_t<3, 512, 1, true>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+        else launch_multi_t<3, 512, 1, false>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+    } else {
+        if (walls) launch_multi_t<2, 256, 2, true>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+        else launch_multi_t<2, 256, 2, false>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+    }
 }
 
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s) {
     const size_t smem = mixed_smem_bytes(a.t, a.g.ndim);
-    if (a.g.ndim == 3) launch_t<3, 512, 1>(a, smem, s);
-    else launch_t<2, 256, 2>(a, smem, s);
+    const bool walls = a.g.bcx == 1;
+    if (a.g.ndim == 3) {
+        if (walls) launch_t<3, 512, 1, true>(a, smem, s);
+        else launch_t<3, 512, 1, false>(a, smem, s);
+    } else {
+        if (walls) launch_t<2, 256, 2, true>(a, smem, s);
+        else launch_t<2, 256, 2, false>(a, smem, s);
+    }
 }
 
 }  // namespace pic

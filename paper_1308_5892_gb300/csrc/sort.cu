@@ -82,20 +82,46 @@ __device__ inline void zero_body(int *a, long long n, int b, int nb) {
     for (long long i = (long long)b * blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) a[i] = 0;
 }
 
+// Keys of the four source elements i + v * step (v = 0..3) of a walk, -1 past its end.
+template <int NDIM>
+__device__ __forceinline__ void walk_keys(const SortArgs &a, const SrcWalk &w, long long i, long long end, int t0,
+                                          int nt, long long nkeys, long long (&p)[4], int (&key)[4]) {
+    uint32_t c[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const long long iv = i + v * w.step();
+        p[v] = iv < end ? w.pos(iv, t0, nt) : -1;
+        c[v] = p[v] >= 0 ? __ldg(a.src.cell + p[v]) : 0u;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        key[v] = p[v] >= 0 ? cell_key<NDIM>(a.t, c[v]) : -1;
+        if (p[v] >= 0 && (key[v] < 0 || key[v] >= nkeys)) {
+            atomicOr(a.err, ERR_SORT);
+            key[v] = -1;
+        }
+    }
+}
+
 template <int NDIM>
 __device__ inline void histogram_body(const SortArgs &a, const SrcWalk &w, long long nkeys) {
     long long i, end;
     int t0, nt;
     w.begin(i, end, t0, nt);
-    for (; i < end; i += w.step()) {
-        const long long p = w.pos(i, t0, nt);
-        const int key = cell_key<NDIM>(a.t, a.src.cell[p]);
-        if (key < 0 || key >= nkeys) { atomicOr(a.err, ERR_SORT); continue; }
-        // warp aggregation: lanes with the same key add once
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, key);
-        const int leader = __ffs(peers) - 1;
-        if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + key, __popc(peers));
+    // four independent loads in flight per thread; the loop is warp-uniform
+    // (every lane takes part in the warp aggregation)
+    const int lane = threadIdx.x & 31;
+    for (long long ib = i - lane; ib < end; ib += 4 * w.step()) {
+        long long p[4];
+        int key[4];
+        walk_keys<NDIM>(a, w, ib + lane, end, t0, nt, nkeys, p, key);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            // warp aggregation: lanes with the same key add once
+            const unsigned peers = __match_any_sync(0xffffffffu, key[v]);
+            const int leader = __ffs(peers) - 1;
+            if (key[v] >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + key[v], __popc(peers));
+        }
     }
 }
 
@@ -178,21 +204,28 @@ __device__ inline void rank_body(const SortArgs &a, const SrcWalk &w, long long 
     long long i, end;
     int t0s, nts;
     w.begin(i, end, t0s, nts);
-    for (; i < end; i += w.step()) {
-        const long long p = w.pos(i, t0s, nts);
-        const int key = cell_key<NDIM>(a.t, a.src.cell[p]);
-        if (key < 0 || key >= nkeys) continue;
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, key);
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(a.counts + key, __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        const int rank = base + __popc(peers & ((1u << lane) - 1u));
-        const int tile = key / a.t.cells_per_tile;
-        const int t0 = a.tile_start[tile], t1 = a.tile_start[tile + 1];
-        a.perm[t0 + interleaved_slot(rank - t0, t1 - t0)] = (int)p;
+    const int lane = threadIdx.x & 31;
+    for (long long ib = i - lane; ib < end; ib += 4 * w.step()) {   // warp-uniform loop
+        long long p[4];
+        int key[4];
+        walk_keys<NDIM>(a, w, ib + lane, end, t0s, nts, nkeys, p, key);
+        int base[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            // lanes that share a key take consecutive slots with one atomic
+            const unsigned peers = __match_any_sync(0xffffffffu, key[v]);
+            const int leader = __ffs(peers) - 1;
+            int b = 0;
+            if (key[v] >= 0 && lane == leader) b = atomicAdd(a.counts + key[v], __popc(peers));
+            base[v] = __shfl_sync(0xffffffffu, b, leader) + __popc(peers & ((1u << lane) - 1u));
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (key[v] < 0) continue;
+            const int tile = key[v] / a.t.cells_per_tile;
+            const int t0 = __ldg(a.tile_start + tile), t1 = __ldg(a.tile_start + tile + 1);
+            a.perm[t0 + interleaved_slot(base[v] - t0, t1 - t0)] = (int)p[v];
+        }
     }
 }
 
@@ -251,7 +284,8 @@ inline int blocks_for(long long n, int threads) {
     return (int)(b < 1 ? 1 : (b < cap ? b : cap));
 }
 __host__ __device__ inline long long nkeys_of(const SortArgs &a) { return (long long)a.t.ntiles * a.t.cells_per_tile; }
-inline int walk_blocks(const SortArgs &a) { return a.old_tile_start ? a.t.ntiles : blocks_for(a.n, 256); }
+constexpr int kWalkThreads = 512;
+inline int walk_blocks(const SortArgs &a) { return a.old_tile_start ? a.t.ntiles : blocks_for(a.n, kWalkThreads); }
 __host__ __device__ inline int scan_blocks(const SortArgs &a) { return (int)((nkeys_of(a) + kScanTile - 1) / kScanTile); }
 inline int key_blocks(const SortArgs &a) { return blocks_for(nkeys_of(a), 256); }
 inline int gather_blocks(const SortArgs &a) { return (int)((a.n + kGatherChunk - 1) / kGatherChunk); }
@@ -357,18 +391,18 @@ size_t sort_scan_scratch(long long nkeys) { return (size_t)((nkeys + kScanTile -
 void launch_sort(const SortArgs &a, cudaStream_t s) {
     k_zero<<<key_blocks(a), 256, 0, s>>>(a);
     if (a.n > 0) {
-        if (a.g.ndim == 3) k_histogram<3><<<walk_blocks(a), 256, 0, s>>>(a);
-        else k_histogram<2><<<walk_blocks(a), 256, 0, s>>>(a);
+        if (a.g.ndim == 3) k_histogram<3><<<walk_blocks(a), kWalkThreads, 0, s>>>(a);
+        else k_histogram<2><<<walk_blocks(a), kWalkThreads, 0, s>>>(a);
     }
     k_scan_blocks<<<scan_blocks(a), kScanThreads, 0, s>>>(a);
     k_scan_sums<<<1, kScanThreads, 0, s>>>(a);
     k_scan_finish<<<key_blocks(a), 256, 0, s>>>(a);
     if (a.n > 0) {
         if (a.g.ndim == 3) {
-            k_rank<3><<<walk_blocks(a), 256, 0, s>>>(a);
+            k_rank<3><<<walk_blocks(a), kWalkThreads, 0, s>>>(a);
             k_gather<3><<<gather_blocks(a), kGatherThreads, 0, s>>>(a);
         } else {
-            k_rank<2><<<walk_blocks(a), 256, 0, s>>>(a);
+            k_rank<2><<<walk_blocks(a), kWalkThreads, 0, s>>>(a);
             k_gather<2><<<gather_blocks(a), kGatherThreads, 0, s>>>(a);
         }
     }
@@ -396,15 +430,15 @@ void launch_sort_multi(const SortArgs *d_args, const int *d_prefix, const int *h
               ng = h_prefix[4 * (nsort + 1) - 1];
     k_zero_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort);
     if (nw > 0) {
-        if (ndim == 3) k_histogram_multi<3><<<nw, 256, 0, s>>>(d_args, pw, nsort);
-        else k_histogram_multi<2><<<nw, 256, 0, s>>>(d_args, pw, nsort);
+        if (ndim == 3) k_histogram_multi<3><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
+        else k_histogram_multi<2><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
     }
     k_scan_blocks_multi<<<nb, kScanThreads, 0, s>>>(d_args, pb, nsort);
     k_scan_sums_multi<<<nsort, kScanThreads, 0, s>>>(d_args);
     k_scan_finish_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort);
     if (nw > 0) {
-        if (ndim == 3) k_rank_multi<3><<<nw, 256, 0, s>>>(d_args, pw, nsort);
-        else k_rank_multi<2><<<nw, 256, 0, s>>>(d_args, pw, nsort);
+        if (ndim == 3) k_rank_multi<3><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
+        else k_rank_multi<2><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
     }
     if (ng > 0) {
         if (ndim == 3) k_gather_multi<3><<<ng, kGatherThreads, 0, s>>>(d_args, pg, nsort);

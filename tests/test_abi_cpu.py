@@ -59,10 +59,7 @@ def test_init_rejects_invalid_descriptors(kw, why):
     assert not h.value
 
 
-def test_init_rejects_conductor_in_mixed_path_and_bad_precision():
-    d = pic.run_desc(2, 16, 16, 1, 2.0, 8.0, 0.5, [(-1.0, 1.0, 10)], bc=(1, 0, 0))
-    st, h = _init(d, precision=pic.PIC_MIXED)
-    assert st == pic.PIC_EINVAL
+def test_init_rejects_bad_precision():
     d = pic.run_desc(2, 16, 16, 1, 2.0, 8.0, 0.5, [(-1.0, 1.0, 10)])
     st, h = _init(d, precision=7)
     assert st == pic.PIC_EINVAL

@@ -17,20 +17,22 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _make(ndim, shape, ppc, seed, spread, amp, colocate, n_x=2.0, rho_sp0=8.0, dt=0.5, species=synth.PAIR):
+def _make(ndim, shape, ppc, seed, spread, amp, colocate, n_x=2.0, rho_sp0=8.0, dt=0.5, species=synth.PAIR,
+          bc=(0, 0, 0)):
     nx, ny, nz = shape
     arr = synth.random_state_arrays(seed, ndim, nx, ny, nz, ppc=ppc, spread=spread, amp_e=amp, amp_b=amp,
                                     colocate=colocate, species=species)
     n = arr["species"][0]["pos"].shape[1]
     desc = pic.run_desc(ndim, nx, ny, nz if ndim == 3 else 1, n_x, rho_sp0, dt,
-                        [(s["q_over_e"], s["m_over_me"], n) for s in arr["species"]])
+                        [(s["q_over_e"], s["m_over_me"], n) for s in arr["species"]], bc=bc)
     fields = np.concatenate([arr["e"], arr["b"]])
     parts = [np.concatenate([s["pos"], s["u"]]) for s in arr["species"]]
     return desc, fields, parts, arr
 
 
 def _oracle_state(desc, fields, parts, arr):
-    st = oracle.State.empty(desc.ndim, desc.nx, desc.ny, desc.nz, desc.dt, desc.n_x, desc.rho_sp0)
+    st = oracle.State.empty(desc.ndim, desc.nx, desc.ny, desc.nz, desc.dt, desc.n_x, desc.rho_sp0,
+                            bc_x=desc.bc[0])
     st.e[:] = fields[:3]
     st.b[:] = fields[3:]
     for s, p in zip(arr["species"], parts):
@@ -112,6 +114,30 @@ def test_fp64_neutral_start_keeps_gauss_to_roundoff():
     assert d["gauss_max"] <= 1e-12 * d["rho_max"]
 
 
+def _walls(parts, nx):
+    """Put particles on and next to both walls, moving into them (App. A.4)."""
+    for p in parts:
+        k = min(8, p.shape[1])
+        p[0, :k] = [0.0, nx, 0.05, nx - 0.05, 0.3, nx - 0.3, 0.0, nx][:k]
+        p[3, :k] = [-1.5, 1.5, -2.0, 2.0, -3.0, 3.0, 0.7, -0.7][:k]
+
+
+@pytest.mark.parametrize("ndim,shape,ppc", [(2, (33, 20, 1), 6), (3, (12, 10, 9), 4)])
+def test_fp64_conductor_walls_match_oracle(ndim, shape, ppc):
+    desc, fields, parts, arr = _make(ndim, shape, ppc, seed=120 + ndim, spread=2.0, amp=0.05, colocate=False,
+                                     bc=(1, 0, 0))
+    _walls(parts, shape[0])
+    with pic.Context([desc], precision=pic.PIC_FP64) as ctx:
+        ctx.set_state(0, fields, parts)
+        st = _oracle_state(desc, fields, parts, arr)
+        for nsteps in (1, 4):
+            ctx.step(nsteps)
+            oracle.step(st, nsteps)
+            f, p, step = ctx.get_state(0)
+            _compare(desc, f, p, st, 1e-12, 1e-12 * max(shape), 1e-12)
+            assert all(q[0].min() >= 0.0 and q[0].max() <= shape[0] for q in p)
+
+
 # ----------------------------------------------------------------- mixed path
 
 def _mixed_roundtrip(desc, fields, parts, arr, **kw):
@@ -159,6 +185,26 @@ def test_mixed_multistep_with_sorting_and_halo_escape(sort_interval):
     oracle.step(st, 12)
     # FP32 vs FP64 over 12 steps: differences grow from 1e-7 per step
     _compare(desc, f, p, st, 2e-4, 1e-4, 2e-4)
+
+
+@pytest.mark.parametrize("ndim,shape,ppc", [(2, (40, 24, 1), 8), (3, (16, 12, 10), 4)])
+def test_mixed_conductor_walls_match_oracle(ndim, shape, ppc):
+    """Conducting walls in x in the mixed path: reflected particles take the
+    two-leg slow path; fields and particles after 1 and after 6 steps."""
+    desc, fields, parts, arr = _make(ndim, shape, ppc, seed=220 + ndim, spread=2.0, amp=0.05, colocate=False,
+                                     bc=(1, 0, 0))
+    _walls(parts, shape[0])
+    ctx, st = _mixed_roundtrip(desc, fields, parts, arr)
+    with ctx:
+        ctx.step(1)
+        f, p, _ = ctx.get_state(0)
+        oracle.step(st)
+        _compare(desc, f, p, st, 1e-5, 2e-6, 1e-5)
+        ctx.step(5)
+        f, p, _ = ctx.get_state(0)
+        oracle.step(st, 5)
+        _compare(desc, f, p, st, 2e-4, 1e-4, 2e-4)
+        assert all(q[0].min() >= 0.0 and q[0].max() <= shape[0] for q in p)
 
 
 def test_mixed_empty_species_and_boundary_positions():

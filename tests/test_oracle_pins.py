@@ -272,6 +272,40 @@ def test_step_conserves_gauss_law_to_roundoff(ndim, bc):
         assert np.abs(r1 - r0).max() <= 1e-12 * rmax
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_conductor_walls_reflect_and_conserve_charge_off_the_wall(ndim):
+    """Conducting walls at x = 0 and x = n_x (App. A.4): particles stay in
+    [0, n_x] with u_x reversed on reflection; the tangential e and the normal
+    b vanish on the wall; the path to the wall and the mirrored remainder are
+    each charge-conserving, so div e - rho~ is unchanged at every node off the
+    wall plane (on it, the zeroed e_y, e_z change div e)."""
+    shape = (10, 9, 8)
+    arr = synth.random_state_arrays(31 + ndim, ndim, *shape, ppc=8, spread=2.0,
+                                    amp_e=0.01, amp_b=0.01, colocate=False)
+    st = oracle.State.empty(ndim, *shape, dt=0.5, n_x=2.0, rho_sp0=8.0, bc_x=oracle.BC_CONDUCTOR)
+    st.e[:] = arr["e"]
+    st.b[:] = arr["b"]
+    for s in arr["species"]:
+        st.species.append(oracle.Species(s["pos"], s["u"], s["q_over_e"], s["m_over_me"]))
+    r0 = oracle.div_e(st) - oracle.rho(st)
+    rmax = max(np.abs(oracle.rho(st, s)).max() for s in range(2))
+    x_before = [sp.pos[0].copy() for sp in st.species]
+    ux_before = [sp.u[0].copy() for sp in st.species]
+    oracle.step(st)
+    reflected = 0
+    for s, sp in enumerate(st.species):
+        assert sp.pos[0].min() >= 0.0 and sp.pos[0].max() <= shape[0]
+        # a particle reflected at a wall comes back with u_x of the other sign
+        flip = np.sign(sp.u[0]) == -np.sign(ux_before[s])
+        reflected += int(flip.sum())
+    assert reflected > 0
+    for c in (1, 2):
+        assert np.all(st.e[c][:, :, 0] == 0.0)
+    assert np.all(st.b[0][:, :, 0] == 0.0)
+    r1 = oracle.div_e(st) - oracle.rho(st)
+    assert np.abs((r1 - r0)[:, :, 1:]).max() <= 1e-12 * rmax
+
+
 def test_colocated_pairs_start_neutral_and_stay_neutral():
     """Pairs loaded on top of each other give rho~ = 0 with e = 0 (Sect. 2.1);
     Gauss's law then holds to round-off for all later steps."""
