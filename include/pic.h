@@ -244,6 +244,11 @@ pic_status pic_energy_history(pic_ctx *ctx, int run, double *out, int64_t max_st
  * of steps the trials used.  No-op for PIC_FP64. */
 pic_status pic_autotune(pic_ctx *ctx, int max_steps, int tile[3], int *sort_interval, int *steps_taken);
 
+/* Replace the PIC_FLAG_* bits of a context, e.g. to time a window with
+ * PIC_FLAG_TIMING (which replays no CUDA graph) and another without it.
+ * Takes effect at the next call; PIC_EINVAL for unknown bits. */
+pic_status pic_set_flags(pic_ctx *ctx, uint32_t flags);
+
 /* Tuning actually used by a context: tile shape, sort interval, halo. */
 pic_status pic_get_tuning(const pic_ctx *ctx, int tile[3], int *sort_interval, int *halo);
 

@@ -29,7 +29,7 @@ ABI_FUNCTIONS = [
     "pic_set_uniform_field", "pic_load_maxwell_juttner", "pic_step", "pic_sync", "pic_diagnostics",
     "pic_energy_history", "pic_get_tuning", "pic_get_counters", "pic_kernel_time", "pic_get_particles",
     "pic_mlp_train", "pic_mlp_set_weights", "pic_mlp_get_weights", "pic_mlp_gradients", "pic_mlp_infer",
-    "pic_mj_sample_marginal", "pic_gauss_residual_static", "pic_autotune",
+    "pic_mj_sample_marginal", "pic_gauss_residual_static", "pic_autotune", "pic_set_flags",
 ]
 MLP_PARAMS = 8641
 
@@ -114,6 +114,7 @@ def lib(build_if_missing=True):
         "pic_get_tuning": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_int)], st),
         "pic_get_counters": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)], st),
+        "pic_set_flags": ([P, ctypes.c_uint32], st),
         "pic_kernel_time": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int64)], st),
         "pic_get_particles": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
@@ -318,6 +319,10 @@ class Context:
         b = ctypes.c_double()
         self._check(self._L.pic_get_counters(self.h, ctypes.byref(n), ctypes.byref(b)))
         return {"launches_per_step": n.value, "bytes_per_particle_step": b.value}
+
+    def set_flags(self, flags):
+        """Replace the PIC_FLAG_* bits (takes effect at the next call)."""
+        self._check(self._L.pic_set_flags(self.h, int(flags)))
 
     def kernel_time(self, kernel_class, reset=False):
         ms = ctypes.c_double()

@@ -57,6 +57,7 @@ struct Run {
     double *acc = nullptr;      // diagnostics accumulators (64 doubles)
     double *hist = nullptr;     // energy history, 8 doubles per step
     int64_t hist_cap = 0, hist_n = 0;
+    long long *hist_idx = nullptr;  // device copy of hist_n, advanced by the e advance (mixed)
     int64_t step = 0;
     double inv_alpha_abs = 1;
 };
@@ -83,6 +84,8 @@ struct pic_ctx {
     std::vector<std::pair<void *, size_t>> allocs;
     std::string err;
     int64_t launches_per_step = 0;
+    int64_t launch_total = 0;        // launches queued by the current pic_step call
+    int64_t graph_launches = 0;      // launches of one replay of the captured period
     double bytes_per_ps = 0;
     // batched ensemble (nruns > 1, mixed): per-run argument tables on the device
     bool multi = false;
@@ -96,6 +99,15 @@ struct pic_ctx {
     int *sort_prefix_dev = nullptr;       // 4 x (nruns + 1) block prefixes of its phases
     std::vector<SortArgs> h_sort;
     std::vector<int> h_sort_prefix;
+    // CUDA graph of one period of steps (mixed path): captured on a private stream,
+    // replayed on the context stream while the host state matches the capture
+    cudaGraphExec_t graph = nullptr;
+    int graph_period = 0;
+    std::vector<long long> graph_sig;
+    cudaStream_t cap_stream = nullptr;
+    bool capturing = false;
+    char *gstage = nullptr;            // pinned per-step copies of the argument tables (ensemble)
+    size_t gstage_stride = 0, gstage_bytes = 0;
     std::vector<FieldRunF> h_fe, h_fp;
     // PIC_FLAG_TIMING: event pairs per kernel class, resolved in pic_kernel_time
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[3];
@@ -141,7 +153,7 @@ struct KTimer {
     int cls;
     cudaEvent_t a = nullptr;
     KTimer(pic_ctx *c, int k) : ctx(c), cls(k) {
-        if (ctx->flags & PIC_FLAG_TIMING) {
+        if ((ctx->flags & PIC_FLAG_TIMING) && !ctx->capturing) {
             a = take_event(ctx);
             cudaEventRecord(a, ctx->stream);
         }
@@ -421,9 +433,11 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     r.acc = (double *)dev_alloc(ctx, sizeof(double) * 64);
     r.hist_cap = kHistCap;
     r.hist = (double *)dev_alloc(ctx, sizeof(double) * 8 * r.hist_cap);
-    if (!r.rho_s || !r.rho_tot || !r.divb || !r.acc || !r.hist)
+    r.hist_idx = (long long *)dev_alloc(ctx, sizeof(long long));
+    if (!r.rho_s || !r.rho_tot || !r.divb || !r.acc || !r.hist || !r.hist_idx)
         return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the diagnostics buffers");
     CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, ctx->stream));
+    CK(cudaMemsetAsync(r.hist_idx, 0, sizeof(long long), ctx->stream));
     for (int s = 0; s < d.nspecies; ++s) {
         SpeciesState &S = r.sp[s];
         S.q_over_e = d.species[s].q_over_e;
@@ -513,7 +527,9 @@ void sort_species(pic_ctx *ctx, Run &r, SpeciesState &S) {
     sort_done(r, S);
 }
 
-MixedStepArgs mixed_args(pic_ctx *ctx, Run &r, double *hslot) {
+HistRef hist_ref(Run &r) { return HistRef{r.hist, r.hist_idx, r.hist_cap}; }
+
+MixedStepArgs mixed_args(pic_ctx *ctx, Run &r) {
     typedef unsigned long long u64;
     MixedStepArgs a;
     a.g = r.g;
@@ -532,12 +548,13 @@ MixedStepArgs mixed_args(pic_ctx *ctx, Run &r, double *hslot) {
     }
     a.dt = (float)r.d.dt;
     a.mode = 0;
-    a.kin_acc = hslot;
+    a.hist = hist_ref(r);
     a.err = ctx->d_err;
     return a;
 }
 
-FieldRunF field_run(Run &r, double *energy) {
+// energy: record the e^2, b^2 sums (first b half advance); inc: advance the history counter (e advance)
+FieldRunF field_run(Run &r, bool energy, bool inc) {
     typedef unsigned long long u64;
     FieldRunF fr;
     fr.g = r.g;
@@ -548,14 +565,27 @@ FieldRunF field_run(Run &r, double *energy) {
         fr.J[c] = jplane<u64>(r, r.jcur, c);
         fr.Z[c] = jplane<u64>(r, 1 - r.jcur, c);
     }
-    fr.energy_acc = energy;
+    fr.hist = energy ? hist_ref(r) : HistRef{nullptr, nullptr, 0};
+    fr.hist_inc = inc ? r.hist_idx : nullptr;
     fr.scale = 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0) * 0x1p-36;
     return fr;
 }
 
+// Host source of an argument-table upload: the table itself, or (slot >= 0,
+// while a graph is captured) its copy in the pinned region of that step, which
+// the captured copy node reads again at every replay.
+const void *host_src(pic_ctx *ctx, int slot, size_t &off, const void *data, size_t bytes) {
+    if (slot < 0) return data;
+    char *dst = ctx->gstage + (size_t)slot * ctx->gstage_stride + off;
+    std::memcpy(dst, data, bytes);
+    off += (bytes + 255) & ~size_t(255);
+    return dst;
+}
+
 // One step of every run of a mixed ensemble: per-run sorts when due, then one
 // batched launch per field phase and one persistent push launch for all runs.
-pic_status step_multi(pic_ctx *ctx) {
+pic_status step_multi(pic_ctx *ctx, int slot) {
+    size_t soff = 0;
     cudaStream_t s = ctx->stream;
     const int nr = (int)ctx->runs.size();
     int launches = 0;
@@ -578,10 +608,11 @@ pic_status step_multi(pic_ctx *ctx) {
                 if (q < r.d.nspecies) ctx->h_sort[ns++] = sort_args(ctx, r, r.sp[q]);
             }
             sort_multi_prefixes(ctx->h_sort.data(), ns, ctx->h_sort_prefix.data());
-            CK(cudaMemcpyAsync(ctx->sort_args_dev, ctx->h_sort.data(), sizeof(SortArgs) * ns, cudaMemcpyHostToDevice,
-                               s));
-            CK(cudaMemcpyAsync(ctx->sort_prefix_dev, ctx->h_sort_prefix.data(), sizeof(int) * 4 * (ns + 1),
-                               cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(ctx->sort_args_dev, host_src(ctx, slot, soff, ctx->h_sort.data(), sizeof(SortArgs) * ns),
+                               sizeof(SortArgs) * ns, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(ctx->sort_prefix_dev,
+                               host_src(ctx, slot, soff, ctx->h_sort_prefix.data(), sizeof(int) * 4 * (ns + 1)),
+                               sizeof(int) * 4 * (ns + 1), cudaMemcpyHostToDevice, s));
             launch_sort_multi(ctx->sort_args_dev, ctx->sort_prefix_dev, ctx->h_sort_prefix.data(), ns,
                               ctx->runs[0].d.ndim, s);
             for (int i : due) {
@@ -604,14 +635,16 @@ pic_status step_multi(pic_ctx *ctx) {
     }
     for (int i = 0; i < nr; ++i) {
         Run &r = ctx->runs[i];
-        double *hslot = (r.hist_n < r.hist_cap) ? r.hist + 8 * r.hist_n : nullptr;
-        ctx->h_args[i] = mixed_args(ctx, r, hslot);
-        ctx->h_fe[i] = field_run(r, hslot ? hslot + 2 : nullptr);
-        ctx->h_fp[i] = field_run(r, nullptr);
+        ctx->h_args[i] = mixed_args(ctx, r);
+        ctx->h_fe[i] = field_run(r, true, false);
+        ctx->h_fp[i] = field_run(r, false, true);
     }
-    CK(cudaMemcpyAsync(ctx->multi_args, ctx->h_args.data(), sizeof(MixedStepArgs) * nr, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->multi_fe, ctx->h_fe.data(), sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->multi_fp, ctx->h_fp.data(), sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->multi_args, host_src(ctx, slot, soff, ctx->h_args.data(), sizeof(MixedStepArgs) * nr),
+                       sizeof(MixedStepArgs) * nr, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->multi_fe, host_src(ctx, slot, soff, ctx->h_fe.data(), sizeof(FieldRunF) * nr),
+                       sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->multi_fp, host_src(ctx, slot, soff, ctx->h_fp.data(), sizeof(FieldRunF) * nr),
+                       sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
     const float dt = (float)ctx->runs[0].d.dt;
     {
         KTimer t(ctx, PIC_KERNEL_FIELD);
@@ -635,7 +668,7 @@ pic_status step_multi(pic_ctx *ctx) {
         r.step++;
         if (r.hist_n < r.hist_cap) r.hist_n++;
     }
-    ctx->launches_per_step = launches + 5;
+    ctx->launch_total += launches + 5;
     ctx->bytes_per_ps = ctx->runs[0].d.ndim == 2 ? 48.0 : 56.0;
     return PIC_OK;
 }
@@ -648,7 +681,7 @@ void step_run(pic_ctx *ctx, Run &r) {
         FieldPtrs<double> f = fields_of<double>(r);
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
-            launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, hslot ? hslot + 2 : nullptr, s);
+            launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, HistRef{hslot, nullptr, 0}, s);
         }
         double *J[3] = {jplane<double>(r, r.jcur, 0), jplane<double>(r, r.jcur, 1), jplane<double>(r, r.jcur, 2)};
         {
@@ -663,11 +696,11 @@ void step_run(pic_ctx *ctx, Run &r) {
         const double *Jc[3] = {J[0], J[1], J[2]};
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
-            launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, nullptr, s);
+            launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, HistRef{nullptr, nullptr, 0}, s);
             launch_e_advance<double>(r.g, f, Jc, Z, r.d.dt, s);
         }
         ctx->bytes_per_ps = r.d.ndim == 2 ? 80.0 : 96.0;
-        ctx->launches_per_step = 3 + nsp;
+        ctx->launch_total += 3 + nsp;
     } else {
         int launches = 0;
         if (!r.sorted || r.since_sort >= r.sort_interval) {
@@ -680,7 +713,7 @@ void step_run(pic_ctx *ctx, Run &r) {
         FieldPtrs<float> f = fields_of<float>(r);
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
-            launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, hslot ? hslot + 2 : nullptr, s);
+            launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, hist_ref(r), s);
             launch_node_fields(r.g, f, r.nfA, r.nfB, s);
         }
         typedef unsigned long long u64;
@@ -704,7 +737,7 @@ void step_run(pic_ctx *ctx, Run &r) {
             }
             a.dt = (float)r.d.dt;
             a.mode = 0;
-            a.kin_acc = hslot;
+            a.hist = hist_ref(r);
             a.err = ctx->d_err;
             launch_push_mixed(a, s);
         }
@@ -712,12 +745,13 @@ void step_run(pic_ctx *ctx, Run &r) {
         const u64 *Jc[3] = {J[0], J[1], J[2]};
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
-            launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, nullptr, s);
-            launch_e_advance_fx(r.g, f, Jc, Z, (float)r.d.dt, 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0), s);
+            launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, HistRef{nullptr, nullptr, 0}, s);
+            launch_e_advance_fx(r.g, f, Jc, Z, (float)r.d.dt, 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0), r.hist_idx,
+                                s);
         }
         r.since_sort++;
         launches += 5;
-        ctx->launches_per_step = launches;
+        ctx->launch_total += launches;
         ctx->bytes_per_ps = r.d.ndim == 2 ? 48.0 : 56.0;
     }
     r.jcur = 1 - r.jcur;
@@ -729,6 +763,124 @@ void step_run(pic_ctx *ctx, Run &r) {
 
 pic_status mlp_load(pic_ctx *ctx, int run, int species, long long n, double theta, const double beta[3], int profile,
                     double L, double x0, int colocate_with, uint64_t seed);
+
+namespace {
+
+pic_status one_step(pic_ctx *ctx, int slot) {
+    if (ctx->multi) return step_multi(ctx, slot);
+    for (auto &r : ctx->runs) step_run(ctx, r);
+    return PIC_OK;
+}
+
+int graph_period_of(const pic_ctx *ctx) { return 2 * std::max(1, ctx->runs[0].sort_interval); }
+
+// A period of 2K steps (K = sort interval) starting with a sort brings every
+// alternating buffer (current planes, particle buffers, tile offsets) back to
+// where it started, so its launches can be replayed as long as each period
+// starts in this phase.
+bool graph_aligned(const pic_ctx *ctx) {
+    if (ctx->multi_tiles_dirty) return false;
+    for (const auto &r : ctx->runs) {
+        if (!r.sorted || r.since_sort < r.sort_interval || r.sort_interval != ctx->runs[0].sort_interval) return false;
+        for (int q = 0; q < r.d.nspecies; ++q)
+            if (!r.sp[q].tiled || r.sp[q].tiled_ntiles != r.t.ntiles) return false;
+    }
+    return true;
+}
+
+// Everything the launches of a period depend on.
+std::vector<long long> graph_signature(const pic_ctx *ctx) {
+    std::vector<long long> v;
+    v.push_back((long long)(uintptr_t)ctx->stream);
+    for (const auto &r : ctx->runs) {
+        v.push_back(r.jcur);
+        v.push_back(r.sort_interval);
+        for (int a = 0; a < 3; ++a) v.push_back(r.t.T[a]);
+        for (int q = 0; q < r.d.nspecies; ++q) {
+            const SpeciesState &S = r.sp[q];
+            v.push_back(S.cur);
+            v.push_back(S.n);
+            v.push_back((long long)(uintptr_t)S.tile_start);
+            v.push_back((long long)(uintptr_t)S.tile_start_alt);
+        }
+    }
+    return v;
+}
+
+// Host counters that do not cycle with the period.
+void advance_counters(pic_ctx *ctx, int P) {
+    for (auto &r : ctx->runs) {
+        r.step += P;
+        r.hist_n = std::min<int64_t>(r.hist_n + P, r.hist_cap);
+    }
+}
+
+struct HostSnapshot {
+    std::vector<Run> runs;
+};
+
+pic_status capture_graph(pic_ctx *ctx) {
+    const int P = graph_period_of(ctx);
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return PIC_ECUDA;
+    const int nr = (int)ctx->runs.size();
+    if (ctx->multi) {
+        int maxsp = 0;
+        for (auto &r : ctx->runs) maxsp = std::max(maxsp, r.d.nspecies);
+        const size_t a = 256;
+        auto up = [a](size_t b) { return (b + a - 1) & ~(a - 1); };
+        const size_t stride = up(sizeof(MixedStepArgs) * nr) + 2 * up(sizeof(FieldRunF) * nr) +
+                              maxsp * (up(sizeof(SortArgs) * nr) + up(sizeof(int) * 4 * (nr + 1)));
+        if (ctx->gstage_bytes < stride * P) {
+            if (ctx->gstage) cudaFreeHost(ctx->gstage);
+            ctx->gstage = nullptr;
+            ctx->gstage_bytes = 0;
+            if (cudaMallocHost((void **)&ctx->gstage, stride * P) != cudaSuccess) return PIC_ENOMEM;
+            ctx->gstage_bytes = stride * P;
+        }
+        ctx->gstage_stride = stride;
+    }
+    // the host bookkeeping of the period is done once, during the capture
+    HostSnapshot snap{ctx->runs};
+    const std::vector<long long> sig = graph_signature(ctx);
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    ctx->capturing = true;
+    const int64_t launches0 = ctx->launch_total;
+    pic_status st = PIC_OK;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = PIC_ECUDA;
+    for (int p = 0; p < P && st == PIC_OK; ++p) st = one_step(ctx, p);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->capturing = false;
+    ctx->stream = user;
+    if (st == PIC_OK && (ec != cudaSuccess || !g)) st = PIC_ECUDA;
+    if (st == PIC_OK && cudaGraphInstantiate(&ctx->graph, g, 0) != cudaSuccess) {
+        ctx->graph = nullptr;
+        st = PIC_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (st != PIC_OK) {
+        cudaGetLastError();   // clear a capture error; nothing was launched
+        ctx->runs = snap.runs;
+        ctx->graph_sig.clear();
+        return st;
+    }
+    // the host state has cycled back; the signature must match for replays
+    if (graph_signature(ctx) != sig) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+        ctx->runs = snap.runs;
+        return PIC_ESTATE;
+    }
+    ctx->graph_sig = sig;
+    ctx->graph_period = P;
+    ctx->graph_launches = ctx->launch_total - launches0;
+    return PIC_OK;
+}
+
+}  // namespace
 
 // ================================================================== ABI
 
@@ -843,6 +995,9 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
 void pic_destroy(pic_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->gstage) cudaFreeHost(ctx->gstage);
     for (int k = 0; k < 3; ++k)
         for (auto &pr : ctx->ev_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
@@ -928,6 +1083,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
     r.step = 0;
     r.hist_n = 0;
     CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, sm));
+    CK(cudaMemsetAsync(r.hist_idx, 0, sizeof(long long), sm));
     return read_err(ctx);
 }
 
@@ -1027,17 +1183,45 @@ pic_status pic_set_uniform_field(pic_ctx *ctx, int run, const double e0[3], cons
 pic_status pic_step(pic_ctx *ctx, int nsteps) {
     if (!ctx) return PIC_EINVAL;
     if (nsteps < 0) return fail(ctx, PIC_EINVAL, "nsteps must be >= 0");
-    for (int n = 0; n < nsteps; ++n) {
-        if (ctx->multi) {
-            pic_status st = step_multi(ctx);
-            if (st) return st;
-        } else {
-            for (auto &r : ctx->runs) step_run(ctx, r);
+    int n = 0;
+    ctx->launch_total = 0;
+    const bool graphs = ctx->precision == PIC_MIXED && !(ctx->flags & (PIC_FLAG_NO_GRAPH | PIC_FLAG_TIMING));
+    while (n < nsteps) {
+        if (graphs && graph_aligned(ctx) && nsteps - n >= graph_period_of(ctx)) {
+            const int P = graph_period_of(ctx);
+            if (!ctx->graph || ctx->graph_sig != graph_signature(ctx)) {
+                if (capture_graph(ctx) != PIC_OK) {
+                    // capture unavailable: launch this period directly
+                    for (int q = 0; q < P; ++q) {
+                        pic_status st = one_step(ctx, -1);
+                        if (st) return st;
+                    }
+                    n += P;
+                    continue;
+                }
+            } else {
+                advance_counters(ctx, P);
+                ctx->launch_total += ctx->graph_launches;
+            }
+            CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            n += P;
+            continue;
         }
+        pic_status st = one_step(ctx, -1);
+        if (st) return st;
+        ++n;
     }
+    if (nsteps > 0) ctx->launches_per_step = (ctx->launch_total + nsteps / 2) / nsteps;
     CK(cudaGetLastError());
     if (ctx->flags & PIC_FLAG_ASYNC) return PIC_OK;
     return read_err(ctx);
+}
+
+pic_status pic_set_flags(pic_ctx *ctx, uint32_t flags) {
+    if (!ctx) return PIC_EINVAL;
+    if (flags & ~(PIC_FLAG_ASYNC | PIC_FLAG_NO_GRAPH | PIC_FLAG_TIMING)) return fail(ctx, PIC_EINVAL, "unknown flag bits");
+    ctx->flags = flags;
+    return PIC_OK;
 }
 
 pic_status pic_sync(pic_ctx *ctx) {
@@ -1202,7 +1386,7 @@ pic_status pic_autotune(pic_ctx *ctx, int max_steps, int tile[3], int *sort_inte
                     apply_tuning(ctx, T, K);
                     CK(cudaEventRecord(e0, ctx->stream));
                     const uint32_t f = ctx->flags;
-                    ctx->flags |= PIC_FLAG_ASYNC;
+                    ctx->flags |= PIC_FLAG_ASYNC | PIC_FLAG_NO_GRAPH;
                     pic_status st = pic_step(ctx, n_trial);
                     ctx->flags = f;
                     if (st) return st;
@@ -1354,6 +1538,7 @@ pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double p
     r.step = 0;
     r.hist_n = 0;
     CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, sm));
+    CK(cudaMemsetAsync(r.hist_idx, 0, sizeof(long long), sm));
     return read_err(ctx);
 }
 
@@ -1452,6 +1637,7 @@ pic_status mlp_load(pic_ctx *ctx, int run, int species, long long n, double thet
     r.step = 0;
     r.hist_n = 0;
     CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, sm));
+    CK(cudaMemsetAsync(r.hist_idx, 0, sizeof(long long), sm));
     return read_err(ctx);
 }
 

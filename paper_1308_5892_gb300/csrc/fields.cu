@@ -85,8 +85,10 @@ __device__ __forceinline__ void b_advance_cell(const Geom &g, const FieldPtrs<R>
 }
 
 template <typename R>
-__global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, double *energy_acc) {
+__global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, HistRef hist) {
     const long long stride = (long long)gridDim.x * blockDim.x;
+    double *slot = hist.slot();
+    double *energy_acc = slot ? slot + 2 : nullptr;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride)
         b_advance_cell<R>(g, f, h, p, energy_acc != nullptr, acc);
@@ -175,7 +177,10 @@ __device__ __forceinline__ void e_fx_cell(const Geom &g, const FieldPtrs<float> 
 
 __global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long long *J0,
                                const unsigned long long *J1, const unsigned long long *J2, unsigned long long *Z0,
-                               unsigned long long *Z1, unsigned long long *Z2, float dt, double scale) {
+                               unsigned long long *Z1, unsigned long long *Z2, float dt, double scale,
+                               long long *hist_inc) {
+    // no kernel of this launch reads the counter; the next step's kernels see the new value
+    if (hist_inc && blockIdx.x == 0 && threadIdx.x == 0) *hist_inc += 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride)
         e_fx_cell(g, f, J0, J1, J2, Z0, Z1, Z2, dt, scale, p);
@@ -248,12 +253,15 @@ __global__ void __launch_bounds__(256) k_fields_multi(const FieldRunF *runs, con
     const long long p = (long long)(blockIdx.x - block_prefix[run_sh]) * blockDim.x + threadIdx.x;
     const bool in = p < r.g.pcells;
     if (PHASE == FIELD_B_HALF) {
+        double *slot = r.hist.slot();
+        double *energy_acc = slot ? slot + 2 : nullptr;
         double acc[6] = {0, 0, 0, 0, 0, 0};
-        if (in) b_advance_cell<float>(r.g, r.f, h, p, r.energy_acc != nullptr, acc);
-        if (r.energy_acc) block_accumulate<6>(acc, r.energy_acc);
+        if (in) b_advance_cell<float>(r.g, r.f, h, p, energy_acc != nullptr, acc);
+        if (energy_acc) block_accumulate<6>(acc, energy_acc);
     } else if (PHASE == FIELD_NODE) {
         if (in) node_cell(r.g, r.f, r.nfA, r.nfB, p);
     } else {
+        if (r.hist_inc && blockIdx.x == block_prefix[run_sh] && threadIdx.x == 0) *r.hist_inc += 1;
         if (in) e_fx_cell(r.g, r.f, r.J[0], r.J[1], r.J[2], r.Z[0], r.Z[1], r.Z[2], dt, r.scale, p);
     }
 }
@@ -281,8 +289,8 @@ inline int grid_for(long long n, int threads) {
 }  // namespace
 
 template <typename R>
-void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, double *energy_acc, cudaStream_t s) {
-    k_b_advance<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, h, energy_acc);
+void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, HistRef energy, cudaStream_t s) {
+    k_b_advance<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, h, energy);
 }
 
 template <typename R>
@@ -304,9 +312,10 @@ void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_
 }
 
 void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long long *const J[3],
-                         unsigned long long *const Jzero[3], float dt, double alpha_abs, cudaStream_t s) {
+                         unsigned long long *const Jzero[3], float dt, double alpha_abs, long long *hist_inc,
+                         cudaStream_t s) {
     k_e_advance_fx<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, J[0], J[1], J[2], Jzero[0], Jzero[1], Jzero[2],
-                                                           dt, alpha_abs * 0x1p-36);
+                                                           dt, alpha_abs * 0x1p-36, hist_inc);
 }
 
 template <typename R>
@@ -315,8 +324,8 @@ void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const
                                                              (R)b0[1], (R)b0[2]);
 }
 
-template void launch_b_advance<float>(const Geom &, FieldPtrs<float>, float, double *, cudaStream_t);
-template void launch_b_advance<double>(const Geom &, FieldPtrs<double>, double, double *, cudaStream_t);
+template void launch_b_advance<float>(const Geom &, FieldPtrs<float>, float, HistRef, cudaStream_t);
+template void launch_b_advance<double>(const Geom &, FieldPtrs<double>, double, HistRef, cudaStream_t);
 template void launch_e_advance<float>(const Geom &, FieldPtrs<float>, const float *const[3], float *const[3], float,
                                       cudaStream_t);
 template void launch_e_advance<double>(const Geom &, FieldPtrs<double>, const double *const[3], double *const[3],

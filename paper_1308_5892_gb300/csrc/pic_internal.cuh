@@ -85,18 +85,37 @@ struct TileGeom {
     int cells_per_tile;
 };
 
+// Energy-history slot of the current step (8 doubles: kinetic at t from both
+// half steps, e^2 and b^2 per component).  With idx set, the slot is base +
+// 8 * (*idx), idx being a device step counter that the e advance increments,
+// so that a captured CUDA graph of several steps can be replayed; without idx
+// the slot is base itself.  A null base records nothing.
+struct HistRef {
+    double *base;
+    const long long *idx;
+    long long cap;
+    __device__ inline double *slot() const {
+        if (!base) return nullptr;
+        if (!idx) return base;
+        const long long i = *idx;
+        return i < cap ? base + 8 * i : nullptr;
+    }
+};
+
 // ---- kernel launchers (implemented in the .cu files) ----
 
 // fields.cu
 template <typename R>
-void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, double *energy_acc, cudaStream_t s);
+void launch_b_advance(const Geom &g, FieldPtrs<R> f, R h, HistRef energy, cudaStream_t s);
 template <typename R>
 void launch_e_advance(const Geom &g, FieldPtrs<R> f, const R *const J[3], R *const Jzero[3], R dt,
                       cudaStream_t s);
 void launch_node_fields(const Geom &g, FieldPtrs<float> f, float4 *nfA, float2 *nfB, cudaStream_t s);
 // e += dt curl b + |alpha| * J for the fixed-point current of the mixed path
+// hist_inc (nullable): the step counter of the energy history, incremented once
 void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long long *const J[3],
-                         unsigned long long *const Jzero[3], float dt, double alpha_abs, cudaStream_t s);
+                         unsigned long long *const Jzero[3], float dt, double alpha_abs, long long *hist_inc,
+                         cudaStream_t s);
 template <typename R>
 void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s);
 
@@ -120,7 +139,7 @@ struct MixedStepArgs {
     double m_over_me[4];
     float dt;
     int mode;                       // 0 step, 1 half step back (momenta only)
-    double *kin_acc;                // 2 doubles: kinetic energy of u^{t-1/2} and u^{t+1/2}
+    HistRef hist;                   // slot[0..1]: kinetic energy of u^{t-1/2} and u^{t+1/2}
     int *err;
 };
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
@@ -136,7 +155,8 @@ struct FieldRunF {
     float2 *nfB;
     const unsigned long long *J[3];
     unsigned long long *Z[3];
-    double *energy_acc;     // e^2, b^2 sums of the step (nullable)
+    HistRef hist;           // slot[2..7]: e^2, b^2 sums of the step (null base: none)
+    long long *hist_inc;    // E_FX phase: step counter of the history, incremented once (nullable)
     double scale;           // |alpha| 2^-36
 };
 enum { FIELD_B_HALF = 0, FIELD_NODE = 1, FIELD_E_FX = 2 };

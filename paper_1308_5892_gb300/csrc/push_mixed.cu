@@ -535,10 +535,11 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
         if (gx < g.px && gy < g.py && gz < g.pz)
             atomicAdd(a.J[comp] + ((long long)gz * g.py + gy) * g.px + gx, (unsigned long long)v);
     }
-    if (a.kin_acc && threadIdx.x < 2) {
+    double *slot = a.hist.slot();
+    if (slot && threadIdx.x < 2) {
         double t = 0.0;
         for (int w = 0; w < WARPS; ++w) t += kin_sh[threadIdx.x][w];
-        atomicAdd(a.kin_acc + threadIdx.x, t);
+        atomicAdd(slot + threadIdx.x, t);
     }
     __syncthreads();   // shared memory is reused by the next tile of a persistent CTA
 }
