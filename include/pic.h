@@ -99,9 +99,10 @@ typedef struct {
  *  precision      PIC_FP64: every quantity in double precision, plain
  *                 one-thread-per-particle kernel with global atomics.
  *                 PIC_MIXED: positions as cell index + FP32 offset, FP32
- *                 momenta and fields, currents accumulated in FP32 with
- *                 compensated summation in shared memory, particles kept
- *                 sorted by tile; FP64 for diagnostics.
+ *                 momenta and fields, currents summed exactly in fixed point
+ *                 (each flux rounded once to 2^-26 of a particle's volume
+ *                 flux, integer sums), particles kept sorted by tile; FP64
+ *                 for diagnostics.
  *  sort_interval  steps between re-sorts in PIC_MIXED (0: chosen by the autotuner)
  *  tile           tile shape in cells (0: chosen by the autotuner)
  *  stream         cudaStream_t to queue work on (NULL: default stream)
@@ -180,7 +181,11 @@ const char *pic_last_error(const pic_ctx *ctx);
 
 /* Upload a state (see pic_state_view).  Positions must lie in the domain,
  * [0, n) per periodic axis and [0, nx] between conductor walls; counts must
- * not exceed the capacities.  Non-finite values give PIC_ENUMERIC. */
+ * not exceed the capacities (PIC_EINVAL before any device work).  Every value
+ * is checked on the device while it is converted: a non-finite value gives
+ * PIC_ENUMERIC and a position outside the domain PIC_EINVAL, after which the
+ * run's state is undefined until the next successful pic_set_state or load.
+ * Host buffers are read during the call only; pinned buffers are copied by DMA. */
 pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in);
 
 /* Download the state into caller buffers (converted to FP64).  A NULL
@@ -216,7 +221,14 @@ pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double p
 /* Advance every run by nsteps steps of the main loop (App. A.3.1).  Queued
  * on the context stream; unless PIC_FLAG_ASYNC, synchronises and reports a
  * device-side error flag (PIC_ESTATE when a particle moved more than one cell
- * in a step, PIC_ETIMEOUT when a bounded wait gave up). */
+ * in a step, PIC_ETIMEOUT when a bounded wait gave up).
+ * PIC_MIXED without PIC_FLAG_NO_GRAPH or PIC_FLAG_TIMING: once the runs are
+ * sorted and a sort is due, one period of 2K steps (K = sort interval) is
+ * captured as a CUDA graph (on a stream of the context's own; the capture
+ * does not run the steps) and launched on the context stream; later periods
+ * replay it while the state it was captured from is unchanged, so results
+ * are bitwise those of direct launches.  A failed capture falls back to
+ * direct launches. */
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
 /* Wait for queued work and report the device-side error flag. */

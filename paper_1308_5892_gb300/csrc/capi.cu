@@ -200,14 +200,36 @@ R *jplane(Run &r, int buf, int c) {
 // ------------------------------------------------------------ conversion kernels
 
 template <typename R>
-__global__ void k_pad_field(Geom g, const double *src, R *dst) {
+__global__ void k_pad_field(Geom g, const double *src, R *dst, int *err) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells;
          p += (long long)gridDim.x * blockDim.x) {
         const int pi = (int)(p % g.px);
         const long long q = p / g.px;
         const int pj = (int)(q % g.py), pk = (int)(q / g.py);
         const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
-        dst[p] = (R)src[((long long)k * g.ny + j) * g.nx + i];
+        const double v = src[((long long)k * g.ny + j) * g.nx + i];
+        if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
+        dst[p] = (R)v;
+    }
+}
+
+// Position x on axis ax inside the domain: [0, n) periodic, [0, n_x] between walls.
+__device__ inline bool in_domain(const Geom &g, int ax, double x) {
+    const double n = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+    return (ax == 0 && g.bcx == 1) ? (x >= 0.0 && x <= n) : (x >= 0.0 && x < n);
+}
+
+// Validation of an uploaded FP64 particle array (the mixed upload checks as it converts).
+__global__ void k_check64(Geom g, Species64 s, long long n, int *err) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(s.u[a][p])) atomicOr(err, ERR_NONFINITE);
+            if (a < g.ndim) {
+                const double x = s.x[a][p];
+                if (!isfinite(x)) atomicOr(err, ERR_NONFINITE);
+                else if (!in_domain(g, a, x)) atomicOr(err, ERR_RANGE);
+            }
+        }
     }
 }
 
@@ -230,16 +252,21 @@ __global__ void k_upload_mixed(Geom g, const double *st, long long m, long long 
         const int n3[3] = {g.nx, g.ny, g.nz};
         for (int ax = 0; ax < g.ndim; ++ax) {
             const double x = st[ax * m + q];
+            if (!isfinite(x) || !in_domain(g, ax, x)) {
+                atomicOr(err, isfinite(x) ? ERR_RANGE : ERR_NONFINITE);
+                continue;   // the state is rejected; keep the stored cell in range
+            }
             double f = floor(x);
             int ci = (int)f;
             float off = (float)(x - f);
             if (off >= 1.0f) { off = 0.0f; ci += 1; }
             if (g.bcx == 1 && ax == 0 && ci >= g.nx) { ci = g.nx - 1; off = 1.0f; }
             else if (ci >= n3[ax]) ci -= n3[ax];
-            if (ci < 0 || ci >= n3[ax]) atomicOr(err, ERR_NONFINITE);
             c[ax] = ci;
             o[ax] = off;
         }
+        for (int a = 3; a < 6; ++a)
+            if (!isfinite(st[a * m + q])) atomicOr(err, ERR_NONFINITE);
         d.cell[a + q] = pack_cell(g.ndim, c[0], c[1], c[2]);
         d.off[0][a + q] = o[0];
         d.off[1][a + q] = o[1];
@@ -489,7 +516,8 @@ pic_status read_err(pic_ctx *ctx) {
         if (e & ERR_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "a bounded device wait gave up");
         if (e & ERR_FAST_MOVE) return fail(ctx, PIC_ESTATE, "a particle moved more than one cell in one step");
         if (e & ERR_SORT) return fail(ctx, PIC_ESTATE, "particle cell outside the grid during sort");
-        if (e & ERR_NONFINITE) return fail(ctx, PIC_ENUMERIC, "non-finite or out-of-domain particle coordinate");
+        if (e & ERR_NONFINITE) return fail(ctx, PIC_ENUMERIC, "non-finite value in the state");
+        if (e & ERR_RANGE) return fail(ctx, PIC_EINVAL, "particle position outside the domain");
     }
     return PIC_OK;
 }
@@ -1017,36 +1045,26 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
     Run &r = ctx->runs[run];
     const Geom &g = r.g;
     const long long ncell = (long long)g.nx * g.ny * g.nz;
-    // host-side validation before any device work
-    for (long long q = 0; q < 6 * ncell; ++q)
-        if (!std::isfinite(in->fields[q])) return fail(ctx, PIC_ENUMERIC, "non-finite field value at %lld", q);
-    const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+    // counts and buffers are checked here; every value is checked on the device as it is converted
     for (int s = 0; s < r.d.nspecies; ++s) {
         const int64_t n = in->count[s];
         if (n < 0 || n > r.sp[s].cap) return fail(ctx, PIC_EINVAL, "species %d: count %lld exceeds capacity", s, (long long)n);
         if (n > 0 && !in->particles[s]) return fail(ctx, PIC_EINVAL, "species %d: null particle buffer", s);
-        const double *P = in->particles[s];
-        for (int a = 0; a < 6; ++a) {
-            if (a == 2 && g.ndim == 2) continue;
-            for (int64_t p = 0; p < n; ++p) {
-                const double v = P[a * n + p];
-                if (!std::isfinite(v)) return fail(ctx, PIC_ENUMERIC, "species %d: non-finite value", s);
-                if (a < 3) {
-                    const bool ok = (a == 0 && g.bcx == 1) ? (v >= 0.0 && v <= L[0]) : (v >= 0.0 && v < L[a]);
-                    if (!ok) return fail(ctx, PIC_EINVAL, "species %d: position %g outside the domain on axis %d", s, v, a);
-                }
-            }
-        }
     }
     cudaStream_t sm = ctx->stream;
+    {
+        // errors of earlier calls do not belong to this one
+        pic_status st0 = read_err(ctx);
+        (void)st0;
+    }
     double *stg = (double *)ctx->staging;
     const size_t rs = real_size(ctx);
     for (int c = 0; c < 6; ++c) {
         CK(cudaMemcpyAsync(stg, in->fields + c * ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, sm));
         if (ctx->precision == PIC_FP64)
-            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (double *)r.F + c * g.pcells);
+            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (double *)r.F + c * g.pcells, ctx->d_err);
         else
-            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (float *)r.F + c * g.pcells);
+            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (float *)r.F + c * g.pcells, ctx->d_err);
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(r.J, 0, 6 * 8 * g.pcells, sm));
@@ -1063,6 +1081,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
                 else CK(cudaMemsetAsync(S.s64.x[a], 0, sizeof(double) * n, sm));
                 CK(cudaMemcpyAsync(S.s64.u[a], P + (3 + a) * n, sizeof(double) * n, cudaMemcpyHostToDevice, sm));
             }
+            if (n > 0) k_check64<<<nblk(n), 256, 0, sm>>>(g, S.s64, n, ctx->d_err);
         } else {
             S.cur = 0;
             S.tiled = false;

@@ -31,6 +31,7 @@ enum : int {
     ERR_TIMEOUT = 2,     // a bounded spin gave up
     ERR_NONFINITE = 4,   // non-finite value met
     ERR_SORT = 8,        // sort bookkeeping overflow
+    ERR_RANGE = 16,      // a particle position outside the domain (state upload)
 };
 
 struct Geom {

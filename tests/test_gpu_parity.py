@@ -207,6 +207,34 @@ def test_mixed_conductor_walls_match_oracle(ndim, shape, ppc):
         assert all(q[0].min() >= 0.0 and q[0].max() <= shape[0] for q in p)
 
 
+@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_MIXED])
+def test_set_state_rejects_bad_values_then_accepts_a_good_state(precision):
+    """Values are validated on the device as they are converted: a non-finite
+    momentum or field gives PIC_ENUMERIC, a position outside the domain
+    PIC_EINVAL; the next valid state is accepted and steps normally."""
+    desc, fields, parts, arr = _make(2, (16, 12, 1), 2, seed=51, spread=0.5, amp=0.01, colocate=False)
+    with pic.Context([desc], precision=precision) as ctx:
+        bad = [p.copy() for p in parts]
+        bad[1][4, 3] = np.nan
+        with pytest.raises(pic.PicError) as e:
+            ctx.set_state(0, fields, bad)
+        assert e.value.status == pic.PIC_ENUMERIC
+        bad = [p.copy() for p in parts]
+        bad[0][1, 5] = 12.0          # y = ny is outside [0, ny)
+        with pytest.raises(pic.PicError) as e:
+            ctx.set_state(0, fields, bad)
+        assert e.value.status == pic.PIC_EINVAL
+        badf = fields.copy()
+        badf[4, 0, 2, 3] = np.inf
+        with pytest.raises(pic.PicError) as e:
+            ctx.set_state(0, badf, parts)
+        assert e.value.status == pic.PIC_ENUMERIC
+        ctx.set_state(0, fields, parts)
+        ctx.step(2)
+        d = ctx.diagnostics(0)
+        assert d["nonfinite"] == 0
+
+
 def test_mixed_empty_species_and_boundary_positions():
     desc, fields, parts, arr = _make(2, (32, 32, 1), 2, seed=5, spread=0.7, amp=0.03, colocate=False)
     n = parts[0].shape[1]
