@@ -35,6 +35,8 @@ struct SpeciesState {
     int *tile_start_alt = nullptr;
     bool tiled = false;         // current layout comes from a sort
     int tiled_ntiles = 0;       // tile count of the geometry that sort used
+    int *counts = nullptr;      // mixed: key histogram / cursors of the sort, zero between sorts
+    bool counted = false;       // the last push filled counts for the next sort
 };
 
 struct Run {
@@ -44,6 +46,7 @@ struct Run {
     int sort_interval = 4;
     int since_sort = 0;
     int max_tiles = 1;          // tile arrays are sized for the autotuner's smallest tile
+    long long max_keys = 1;     // sort keys of the largest candidate geometry
     bool sorted = false;
     void *F = nullptr;          // 6 planes of Real (e_x..b_z), padded
     void *J = nullptr;          // 2 buffers x 3 planes, padded: double (FP64) or int64 fixed point (mixed)
@@ -51,7 +54,7 @@ struct Run {
     float4 *nfA = nullptr;      // node fields {E_x,E_y,E_z,B_x} (mixed)
     float2 *nfB = nullptr;      // node fields {B_y,B_z} (mixed)
     SpeciesState sp[PIC_MAX_SPECIES];
-    int *counts = nullptr, *offsets = nullptr, *block_sums = nullptr;
+    int *offsets = nullptr, *block_sums = nullptr;
     int *perm = nullptr;        // sort scratch, max species capacity
     double *rho_s = nullptr, *rho_tot = nullptr, *divb = nullptr;
     double *acc = nullptr;      // diagnostics accumulators (64 doubles)
@@ -378,6 +381,14 @@ TileGeom make_tile_geom(const pic_run_desc &d, const int Tin[3], int H) {
     t.H = H;
     t.ntiles = t.ntile[0] * t.ntile[1] * t.ntile[2];
     t.cells_per_tile = t.T[0] * t.T[1] * t.T[2];
+    bool pow2 = true;
+    for (int a = 0; a < 3; ++a) {
+        int lg = 0;
+        while ((1 << lg) < t.T[a]) ++lg;
+        t.lg[a] = lg;
+        if ((1 << lg) != t.T[a]) pow2 = false;
+    }
+    if (!pow2) t.lg[0] = t.lg[1] = t.lg[2] = -1;
     return t;
 }
 
@@ -386,7 +397,7 @@ std::vector<std::vector<int>> tile_candidates(int ndim) {
     if (ndim == 2) return {{16, 16, 1}, {32, 16, 1}, {32, 32, 1}, {16, 8, 1}};
     return {{8, 8, 8}, {8, 8, 4}, {16, 8, 4}};
 }
-std::vector<int> sort_candidates(int ndim) { return ndim == 2 ? std::vector<int>{8, 4, 16} : std::vector<int>{2, 1, 4}; }
+std::vector<int> sort_candidates(int ndim) { return ndim == 2 ? std::vector<int>{8, 4, 16} : std::vector<int>{2, 3, 1, 4}; }
 
 void choose_tiles(Run &r, const pic_opts *o, int &max_tiles, long long &max_keys) {
     const pic_run_desc &d = r.d;
@@ -444,14 +455,14 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
         r.nfA = (float4 *)dev_alloc(ctx, sizeof(float4) * g.pcells);
         r.nfB = (float2 *)dev_alloc(ctx, sizeof(float2) * g.pcells);
         const long long nkeys = max_keys;
-        r.counts = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.offsets = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.block_sums = (int *)dev_alloc(ctx, sizeof(int) * sort_scan_scratch(nkeys));
         r.max_tiles = max_tiles;
+        r.max_keys = max_keys;
         int64_t capmax = 1;
         for (int s = 0; s < d.nspecies; ++s) capmax = std::max<int64_t>(capmax, d.species[s].capacity);
         r.perm = (int *)dev_alloc(ctx, sizeof(int) * capmax);
-        if (!r.nfA || !r.nfB || !r.counts || !r.offsets || !r.block_sums || !r.perm)
+        if (!r.nfA || !r.nfB || !r.offsets || !r.block_sums || !r.perm)
             return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the tile buffers");
     }
     r.rho_s = (double *)dev_alloc(ctx, sizeof(double) * ncell);
@@ -492,6 +503,9 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
                 }
                 if (!m.cell || !m.id) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for particles");
             }
+            S.counts = (int *)dev_alloc(ctx, sizeof(int) * (r.max_keys + 1));
+            if (!S.counts) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the sort counts");
+            CK(cudaMemsetAsync(S.counts, 0, sizeof(int) * (r.max_keys + 1), ctx->stream));
             S.tile_start = (int *)dev_alloc(ctx, sizeof(int) * (r.max_tiles + 1));
             S.tile_start_alt = (int *)dev_alloc(ctx, sizeof(int) * (r.max_tiles + 1));
             if (!S.tile_start || !S.tile_start_alt) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for tile offsets");
@@ -524,6 +538,21 @@ pic_status read_err(pic_ctx *ctx) {
 
 // ------------------------------------------------------------ stepping
 
+// Invariant: at a push, counts are zero unless counted.  Sorts leave them
+// zero, and every other change of the particles or of the tile geometry is
+// followed by a sort before the next push.  Counts left by an earlier
+// counting push whose sort never came (the sort interval grew in between) no
+// longer describe the particles, so they are cleared here.
+void prepare_counts(pic_ctx *ctx, Run &r) {
+    for (int q = 0; q < r.d.nspecies; ++q) {
+        SpeciesState &S = r.sp[q];
+        if (!S.counted) continue;
+        (void)cudaMemsetAsync(S.counts, 0, sizeof(int) * ((size_t)r.t.ntiles * r.t.cells_per_tile + 1),
+                              ctx->stream);   // a failure surfaces at the step's error check
+        S.counted = false;
+    }
+}
+
 SortArgs sort_args(pic_ctx *ctx, Run &r, SpeciesState &S) {
     SortArgs a;
     a.g = r.g;
@@ -531,7 +560,8 @@ SortArgs sort_args(pic_ctx *ctx, Run &r, SpeciesState &S) {
     a.n = S.n;
     a.src = S.mb[S.cur];
     a.dst = S.mb[1 - S.cur];
-    a.counts = r.counts;
+    a.counts = S.counts;
+    a.counted = S.counted ? 1 : 0;
     a.offsets = r.offsets;
     a.block_sums = r.block_sums;
     // the old-tile walk is valid only for the tile geometry the layout was sorted with
@@ -544,6 +574,7 @@ SortArgs sort_args(pic_ctx *ctx, Run &r, SpeciesState &S) {
 
 // Host bookkeeping after the sort of S was enqueued: the sorted copy becomes current.
 void sort_done(Run &r, SpeciesState &S) {
+    S.counted = false;
     S.cur = 1 - S.cur;
     std::swap(S.tile_start, S.tile_start_alt);
     S.tiled = true;
@@ -578,6 +609,7 @@ MixedStepArgs mixed_args(pic_ctx *ctx, Run &r) {
     a.mode = 0;
     a.hist = hist_ref(r);
     a.err = ctx->d_err;
+    for (int q = 0; q < 4; ++q) a.key_counts[q] = nullptr;
     return a;
 }
 
@@ -647,7 +679,7 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
                 Run &r = ctx->runs[i];
                 if (q < r.d.nspecies) sort_done(r, r.sp[q]);
             }
-            launches += 7;
+            launches += 8;
         }
         for (int i : due) {
             ctx->runs[i].sorted = true;
@@ -661,9 +693,16 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         CK(cudaStreamSynchronize(s));
         ctx->multi_tiles_dirty = false;
     }
+    // when the next step sorts every run, this push counts their key histograms
+    bool count = true;
+    for (auto &r : ctx->runs)
+        if (!(r.since_sort + 1 >= r.sort_interval && r.t.lg[0] >= 0)) count = false;
+    for (auto &r : ctx->runs) prepare_counts(ctx, r);
     for (int i = 0; i < nr; ++i) {
         Run &r = ctx->runs[i];
         ctx->h_args[i] = mixed_args(ctx, r);
+        if (count)
+            for (int q = 0; q < r.d.nspecies; ++q) ctx->h_args[i].key_counts[q] = r.sp[q].counts;
         ctx->h_fe[i] = field_run(r, true, false);
         ctx->h_fp[i] = field_run(r, false, true);
     }
@@ -683,7 +722,10 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         KTimer t(ctx, PIC_KERNEL_PUSH);
         CK(cudaMemsetAsync(ctx->multi_counter, 0, sizeof(int), s));
         launch_push_mixed_multi(ctx->multi_args, ctx->multi_tiles, nr, ctx->runs[0].d.ndim, ctx->runs[0].t,
-                                ctx->runs[0].g.bcx == 1, ctx->multi_counter, s);
+                                ctx->runs[0].g.bcx == 1, count, ctx->multi_counter, s);
+        if (count)
+            for (auto &r : ctx->runs)
+                for (int q = 0; q < r.d.nspecies; ++q) r.sp[q].counted = true;
     }
     {
         KTimer t(ctx, PIC_KERNEL_FIELD);
@@ -733,10 +775,12 @@ void step_run(pic_ctx *ctx, Run &r) {
         int launches = 0;
         if (!r.sorted || r.since_sort >= r.sort_interval) {
             KTimer t(ctx, PIC_KERNEL_SORT);
-            for (int q = 0; q < nsp; ++q) sort_species(ctx, r, r.sp[q]);
+            for (int q = 0; q < nsp; ++q) {
+                launches += r.sp[q].counted ? 6 : 8;
+                sort_species(ctx, r, r.sp[q]);
+            }
             r.sorted = true;
             r.since_sort = 0;
-            launches += 7 * nsp;
         }
         FieldPtrs<float> f = fields_of<float>(r);
         {
@@ -767,7 +811,13 @@ void step_run(pic_ctx *ctx, Run &r) {
             a.mode = 0;
             a.hist = hist_ref(r);
             a.err = ctx->d_err;
+            // when the next step sorts, this push counts its key histogram
+            const bool count = r.since_sort + 1 >= r.sort_interval && r.t.lg[0] >= 0;
+            prepare_counts(ctx, r);
+            for (int q = 0; q < 4; ++q) a.key_counts[q] = (count && q < nsp) ? r.sp[q].counts : nullptr;
             launch_push_mixed(a, s);
+            if (count)
+                for (int q = 0; q < nsp; ++q) r.sp[q].counted = true;
         }
         u64 *Z[3] = {jplane<u64>(r, 1 - r.jcur, 0), jplane<u64>(r, 1 - r.jcur, 1), jplane<u64>(r, 1 - r.jcur, 2)};
         const u64 *Jc[3] = {J[0], J[1], J[2]};
@@ -827,6 +877,7 @@ std::vector<long long> graph_signature(const pic_ctx *ctx) {
         for (int q = 0; q < r.d.nspecies; ++q) {
             const SpeciesState &S = r.sp[q];
             v.push_back(S.cur);
+            v.push_back(S.counted);
             v.push_back(S.n);
             v.push_back((long long)(uintptr_t)S.tile_start);
             v.push_back((long long)(uintptr_t)S.tile_start_alt);
@@ -1085,6 +1136,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
         } else {
             S.cur = 0;
             S.tiled = false;
+            S.counted = false;
             const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
             for (int64_t a0 = 0; a0 < n; a0 += chunk) {
                 const int64_t m = std::min(chunk, n - a0);
@@ -1354,7 +1406,10 @@ void apply_tuning(pic_ctx *ctx, const int T[3], int K) {
         r.sort_interval = K;
         if (!same) {
             r.sorted = false;
-            for (int q = 0; q < r.d.nspecies; ++q) r.sp[q].tiled = false;
+            for (int q = 0; q < r.d.nspecies; ++q) {
+                r.sp[q].tiled = false;
+                r.sp[q].counted = false;
+            }
         }
     }
     ctx->multi_tiles_dirty = true;
@@ -1541,6 +1596,7 @@ pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double p
     CK(cudaGetLastError());
     S.n = n;
     S.tiled = false;
+    S.counted = false;
     r.sorted = false;
     r.since_sort = 0;
     // initial staggering of the momenta: one Boris step of -dt/2 (App. A.3.1)
@@ -1641,6 +1697,7 @@ pic_status mlp_load(pic_ctx *ctx, int run, int species, long long n, double thet
     CK(cudaGetLastError());
     S.n = n;
     S.tiled = false;
+    S.counted = false;
     r.sorted = false;
     r.since_sort = 0;
     if (mixed) {

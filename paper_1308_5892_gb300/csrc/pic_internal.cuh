@@ -84,7 +84,16 @@ struct TileGeom {
     int ntile[3];    // tiles per axis
     int ntiles;
     int cells_per_tile;
+    int lg[3];       // log2 T per axis when every T is a power of two, else -1
 };
+
+// Sort key of a cell: tile index * cells_per_tile + index inside the tile
+// (tiles with power-of-two sides only, t.lg[0] >= 0).
+__host__ __device__ inline int tile_key_pow2(const TileGeom &t, int i, int j, int k) {
+    const int ti = i >> t.lg[0], tj = j >> t.lg[1], tk = k >> t.lg[2];
+    const int li = i & (t.T[0] - 1), lj = j & (t.T[1] - 1), lk = k & (t.T[2] - 1);
+    return ((tk * t.ntile[1] + tj) * t.ntile[0] + ti) * t.cells_per_tile + (((lk << t.lg[1]) + lj) << t.lg[0]) + li;
+}
 
 // Energy-history slot of the current step (8 doubles: kinetic at t from both
 // half steps, e^2 and b^2 per component).  With idx set, the slot is base +
@@ -142,11 +151,15 @@ struct MixedStepArgs {
     int mode;                       // 0 step, 1 half step back (momenta only)
     HistRef hist;                   // slot[0..1]: kinetic energy of u^{t-1/2} and u^{t+1/2}
     int *err;
+    // when non-null: per species, the push adds to key_counts[s][key] the number of
+    // particles whose new cell has that sort key (the next sort's histogram)
+    int *key_counts[4];
 };
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
 // persistent launch over the tiles of many runs (same ndim and tile shape)
+// count: every run's args carry key_counts (the next sort's histogram)
 void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
-                             const TileGeom &t, bool walls, int *counter, cudaStream_t s);
+                             const TileGeom &t, bool walls, bool count, int *counter, cudaStream_t s);
 
 // fields.cu, batched over runs: one launch updates every run's grid
 struct FieldRunF {
@@ -182,6 +195,7 @@ struct SortArgs {
     const int *old_tile_start;  // tile offsets of the source layout, or nullptr if untiled
     int *perm;       // n scratch: source index of every destination slot
     int *err;
+    int counted;     // counts already hold the key histogram of src (counted by the push)
 };
 void launch_sort(const SortArgs &a, cudaStream_t s);
 // many independent sorts in one launch per phase: h_prefix (4 x (nsort + 1) ints)

@@ -340,7 +340,7 @@ __device__ __forceinline__ void drain_one(const int *q_base, const float *q_d, c
 }
 
 // All species of one tile of one run (the body of both launch forms below).
-template <int NDIM, int THREADS, bool WALLS>
+template <int NDIM, int THREADS, bool WALLS, bool HIST>
 __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile) {
     extern __shared__ float4 smem4[];
     constexpr int WARPS = THREADS / 32;
@@ -430,6 +430,7 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
             const int base = item < nblk ? pbeg + (item << 10) : pbeg + (nblk << 10) + ((item - nblk) << 5);
             const int kn = item < nblk ? 32 : 1;
             float kin0 = 0.f, kin1 = 0.f;
+            int hk = -1, hn = 0;   // HIST: sort key of the lane's current run of particles, and its length
 #pragma unroll
             for (int j = 0; j < kStages - 1; ++j) issue(base, j, kn);
 #pragma unroll 1
@@ -455,6 +456,18 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                     P.off[1][p] = d[1];
                     if (NDIM == 3) P.off[2][p] = d[2];
                     P.u[0][p] = u[0]; P.u[1][p] = u[1]; P.u[2][p] = u[2];
+                    if (HIST) {
+                        // histogram of the next sort: consecutive particles of a lane mostly share a key
+                        int ki, kj, kk;
+                        unpack_cell(NDIM, c, ki, kj, kk);
+                        const int key = tile_key_pow2(a.t, ki, kj, kk);
+                        if (key != hk) {
+                            if (hn) atomicAdd(a.key_counts[sp] + hk, hn);
+                            hk = key;
+                            hn = 0;
+                        }
+                        ++hn;
+                    }
                     if (fast) {
                         // the start-cell piece goes to the register accumulator
                         if (acc.q0 != q0) {
@@ -502,6 +515,7 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                     }
                 }
             }
+            if (HIST && hn) atomicAdd(a.key_counts[sp] + hk, hn);
             // kinetic energy of the item (at most 32 values per lane in FP32), summed per warp in FP64
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -546,16 +560,16 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
 
 // One CTA per tile of one run; WALLS: conducting walls in x (a separate
 // instantiation keeps their register cost out of the periodic kernel).
-template <int NDIM, int THREADS, int MINB, bool WALLS>
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(MixedStepArgs a) {
-    push_tile<NDIM, THREADS, WALLS>(a, blockIdx.x);
+    push_tile<NDIM, THREADS, WALLS, HIST>(a, blockIdx.x);
 }
 
 // Persistent form for a batch of independent runs of uneven size: resident
 // CTAs take (run, tile) work items from one counter until all tiles of all
 // runs are done, so small runs do not leave most of the GPU idle.
 // tile_prefix[r] is the number of tiles of runs 0..r-1.
-template <int NDIM, int THREADS, int MINB, bool WALLS>
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedStepArgs *runs, const int *tile_prefix,
                                                                     int nruns, int *counter) {
     __shared__ int item_sh;
@@ -575,7 +589,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedS
         int *dst = reinterpret_cast<int *>(&args_sh);
         for (int q = threadIdx.x; q < (int)(sizeof(MixedStepArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
         __syncthreads();
-        push_tile<NDIM, THREADS, WALLS>(args_sh, item - tile_prefix[lo]);
+        push_tile<NDIM, THREADS, WALLS, HIST>(args_sh, item - tile_prefix[lo]);
     }
 }
 
@@ -596,9 +610,9 @@ __global__ void k_half_back_mixed(Geom g, const float4 *nfA, const float2 *nfB, 
     }
 }
 
-template <int NDIM, int THREADS, int MINB, bool WALLS>
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 void launch_t(const MixedStepArgs &a, size_t smem, cudaStream_t s) {
-    auto k = k_push_mixed<NDIM, THREADS, MINB, WALLS>;
+    auto k = k_push_mixed<NDIM, THREADS, MINB, WALLS, HIST>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<a.t.ntiles, THREADS, smem, s>>>(a);
 }
@@ -620,10 +634,10 @@ void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB,
     else k_half_back_mixed<2><<<blocks, 256, 0, s>>>(g, nfA, nfB, sp, n, h, dt);
 }
 
-template <int NDIM, int THREADS, int MINB, bool WALLS>
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem,
                     cudaStream_t s) {
-    auto k = k_push_mixed_multi<NDIM, THREADS, MINB, WALLS>;
+    auto k = k_push_mixed_multi<NDIM, THREADS, MINB, WALLS, HIST>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
@@ -633,28 +647,41 @@ void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns
     k<<<std::max(1, per_sm) * sms, THREADS, smem, s>>>(runs, tile_prefix, nruns, counter);
 }
 
-void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
-                             const TileGeom &t, bool walls, int *counter, cudaStream_t s) {
-    const size_t smem = mixed_smem_bytes(t, ndim);
-    if (ndim == 3) {
-        if (walls) launch_multi_t<3, 512, 1, true>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
-        else launch_multi_t<3, 512, 1, false>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+template <int NDIM, int THREADS, int MINB>
+void launch_multi_dim(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem,
+                      bool walls, bool count, cudaStream_t s) {
+    if (walls) {
+        if (count) launch_multi_t<NDIM, THREADS, MINB, true, true>(runs, tile_prefix, nruns, counter, smem, s);
+        else launch_multi_t<NDIM, THREADS, MINB, true, false>(runs, tile_prefix, nruns, counter, smem, s);
     } else {
-        if (walls) launch_multi_t<2, 256, 2, true>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
-        else launch_multi_t<2, 256, 2, false>(runs_dev, tile_prefix_dev, nruns, counter, smem, s);
+        if (count) launch_multi_t<NDIM, THREADS, MINB, false, true>(runs, tile_prefix, nruns, counter, smem, s);
+        else launch_multi_t<NDIM, THREADS, MINB, false, false>(runs, tile_prefix, nruns, counter, smem, s);
+    }
+}
+
+void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
+                             const TileGeom &t, bool walls, bool count, int *counter, cudaStream_t s) {
+    const size_t smem = mixed_smem_bytes(t, ndim);
+    if (ndim == 3) launch_multi_dim<3, 512, 1>(runs_dev, tile_prefix_dev, nruns, counter, smem, walls, count, s);
+    else launch_multi_dim<2, 256, 2>(runs_dev, tile_prefix_dev, nruns, counter, smem, walls, count, s);
+}
+
+template <int NDIM, int THREADS, int MINB>
+void launch_dim(const MixedStepArgs &a, size_t smem, cudaStream_t s) {
+    const bool walls = a.g.bcx == 1, count = a.key_counts[0] != nullptr;
+    if (walls) {
+        if (count) launch_t<NDIM, THREADS, MINB, true, true>(a, smem, s);
+        else launch_t<NDIM, THREADS, MINB, true, false>(a, smem, s);
+    } else {
+        if (count) launch_t<NDIM, THREADS, MINB, false, true>(a, smem, s);
+        else launch_t<NDIM, THREADS, MINB, false, false>(a, smem, s);
     }
 }
 
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s) {
     const size_t smem = mixed_smem_bytes(a.t, a.g.ndim);
-    const bool walls = a.g.bcx == 1;
-    if (a.g.ndim == 3) {
-        if (walls) launch_t<3, 512, 1, true>(a, smem, s);
-        else launch_t<3, 512, 1, false>(a, smem, s);
-    } else {
-        if (walls) launch_t<2, 256, 2, true>(a, smem, s);
-        else launch_t<2, 256, 2, false>(a, smem, s);
-    }
+    if (a.g.ndim == 3) launch_dim<3, 512, 1>(a, smem, s);
+    else launch_dim<2, 256, 2>(a, smem, s);
 }
 
 }  // namespace pic

@@ -189,7 +189,11 @@ __device__ inline void scan_sums_body(int *block_sums, int nb, int *sh) {
 // Add block offsets; copy to the cursors (counts array); extract tile offsets.
 __device__ inline void scan_finish_body(const SortArgs &a, long long nkeys, int b, int nb) {
     for (long long i = (long long)b * blockDim.x + threadIdx.x; i < nkeys; i += (long long)nb * blockDim.x) {
-        const int v = a.offsets[i] + a.block_sums[i / kScanTile];
+        int v = a.offsets[i] + a.block_sums[i / kScanTile];
+        if (v < 0 || v > a.n) {   // counts inconsistent with the particles: flag, keep offsets in range
+            atomicOr(a.err, ERR_SORT);
+            v = v < 0 ? 0 : (int)a.n;
+        }
         a.offsets[i] = v;
         a.counts[i] = v;
         if (i % a.t.cells_per_tile == 0) a.tile_start[i / a.t.cells_per_tile] = v;
@@ -224,7 +228,9 @@ __device__ inline void rank_body(const SortArgs &a, const SrcWalk &w, long long 
             if (key[v] < 0) continue;
             const int tile = key[v] / a.t.cells_per_tile;
             const int t0 = __ldg(a.tile_start + tile), t1 = __ldg(a.tile_start + tile + 1);
-            a.perm[t0 + interleaved_slot(base[v] - t0, t1 - t0)] = (int)p[v];
+            const long long dst = (long long)t0 + interleaved_slot(base[v] - t0, t1 - t0);
+            if (base[v] >= t0 && base[v] < t1 && dst < a.n) a.perm[dst] = (int)p[v];
+            else atomicOr(a.err, ERR_SORT);   // counts inconsistent with the particles
         }
     }
 }
@@ -336,9 +342,11 @@ __device__ inline int find_sort(const int *prefix, int nsort, int B) {
     return lo;
 }
 
-__global__ void k_zero_multi(const SortArgs *as, const int *prefix, int nsort) {
+// always: zero the counts of every sort (after its rank pass); otherwise skip sorts counted by the push
+__global__ void k_zero_multi(const SortArgs *as, const int *prefix, int nsort, int always) {
     const int s = find_sort(prefix, nsort, blockIdx.x);
     const SortArgs &a = as[s];
+    if (a.counted && !always) return;
     zero_body(a.counts, nkeys_of(a), blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]);
 }
 
@@ -346,6 +354,7 @@ template <int NDIM>
 __global__ void k_histogram_multi(const SortArgs *as, const int *prefix, int nsort) {
     const int s = find_sort(prefix, nsort, blockIdx.x);
     const SortArgs &a = as[s];
+    if (a.counted) return;
     const SrcWalk w{a.old_tile_start, a.n, (int)blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]};
     histogram_body<NDIM>(a, w, nkeys_of(a));
 }
@@ -389,8 +398,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_multi(const SortArgs 
 size_t sort_scan_scratch(long long nkeys) { return (size_t)((nkeys + kScanTile - 1) / kScanTile + 1); }
 
 void launch_sort(const SortArgs &a, cudaStream_t s) {
-    k_zero<<<key_blocks(a), 256, 0, s>>>(a);
-    if (a.n > 0) {
+    if (!a.counted) k_zero<<<key_blocks(a), 256, 0, s>>>(a);
+    if (a.n > 0 && !a.counted) {
         if (a.g.ndim == 3) k_histogram<3><<<walk_blocks(a), kWalkThreads, 0, s>>>(a);
         else k_histogram<2><<<walk_blocks(a), kWalkThreads, 0, s>>>(a);
     }
@@ -406,6 +415,8 @@ void launch_sort(const SortArgs &a, cudaStream_t s) {
             k_gather<2><<<gather_blocks(a), kGatherThreads, 0, s>>>(a);
         }
     }
+    // the counts end zeroed, ready for a push that counts the next sort's histogram
+    k_zero<<<key_blocks(a), 256, 0, s>>>(a);
 }
 
 void sort_multi_prefixes(const SortArgs *h_args, int nsort, int *h_prefix) {
@@ -428,7 +439,7 @@ void launch_sort_multi(const SortArgs *d_args, const int *d_prefix, const int *h
               *pg = d_prefix + 3 * (nsort + 1);
     const int nz = h_prefix[nsort], nw = h_prefix[2 * (nsort + 1) - 1], nb = h_prefix[3 * (nsort + 1) - 1],
               ng = h_prefix[4 * (nsort + 1) - 1];
-    k_zero_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort);
+    k_zero_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort, 0);
     if (nw > 0) {
         if (ndim == 3) k_histogram_multi<3><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
         else k_histogram_multi<2><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
@@ -440,6 +451,8 @@ void launch_sort_multi(const SortArgs *d_args, const int *d_prefix, const int *h
         if (ndim == 3) k_rank_multi<3><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
         else k_rank_multi<2><<<nw, kWalkThreads, 0, s>>>(d_args, pw, nsort);
     }
+    // the counts end zeroed, ready for a push that counts the next sort's histogram
+    k_zero_multi<<<nz, 256, 0, s>>>(d_args, pz, nsort, 1);
     if (ng > 0) {
         if (ndim == 3) k_gather_multi<3><<<ng, kGatherThreads, 0, s>>>(d_args, pg, nsort);
         else k_gather_multi<2><<<ng, kGatherThreads, 0, s>>>(d_args, pg, nsort);
