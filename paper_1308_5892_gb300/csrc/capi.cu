@@ -53,6 +53,8 @@ struct Run {
     int jcur = 0;
     float4 *nfA = nullptr;      // node fields {E_x,E_y,E_z,B_x} (mixed)
     float2 *nfB = nullptr;      // node fields {B_y,B_z} (mixed)
+    bool tma = false;           // TMA descriptors of nfA/nfB for the current tile box are valid
+    CUtensorMap tmA{}, tmB{};
     SpeciesState sp[PIC_MAX_SPECIES];
     int *offsets = nullptr, *block_sums = nullptr;
     int *perm = nullptr;        // sort scratch, max species capacity
@@ -425,6 +427,55 @@ void choose_tiles(Run &r, const pic_opts *o, int &max_tiles, long long &max_keys
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// TMA descriptors of the node-field arrays with a box of one tile + halo.  The
+// arrays are FP32 planes of 4 (nfA) and 2 (nfB) floats per padded node; a copy
+// starts at x = 4 x0 and 2 x0 floats, so the rules (inner box and strides
+// multiples of 16 bytes, start x times 4 bytes a multiple of 16) need an even
+// tile width and an even padded x extent.  Otherwise r.tma stays false and the
+// push stages with coalesced loads.
+void node_maps(Run &r) {
+    r.tma = false;
+    EncodeTiledFn enc = encode_tiled();
+    const Geom &g = r.g;
+    const TileGeom &t = r.t;
+    if (!enc || !r.nfA || (t.T[0] & 1) || (g.px & 1) || t.R[0] * 4 > 256 || t.R[1] > 256 || t.R[2] > 256) return;
+    const cuuint32_t rank = g.ndim == 3 ? 3 : 2;
+    for (int which = 0; which < 2; ++which) {
+        const cuuint64_t per = which == 0 ? 4 : 2;   // floats per node
+        const cuuint64_t dims[3] = {per * (cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)g.pz};
+        const cuuint64_t strides[2] = {per * 4 * (cuuint64_t)g.px, per * 4 * (cuuint64_t)g.px * g.py};
+        const cuuint32_t box[3] = {(cuuint32_t)(per * t.R[0]), (cuuint32_t)t.R[1], (cuuint32_t)t.R[2]};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        void *base = which == 0 ? (void *)r.nfA : (void *)r.nfB;
+        CUtensorMap *m = which == 0 ? &r.tmA : &r.tmB;
+        if (enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    }
+    r.tma = true;
+}
+
 pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     const pic_run_desc &d = r.d;
     const bool mixed = ctx->precision == PIC_MIXED;
@@ -454,6 +505,7 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     if (mixed) {
         r.nfA = (float4 *)dev_alloc(ctx, sizeof(float4) * g.pcells);
         r.nfB = (float2 *)dev_alloc(ctx, sizeof(float2) * g.pcells);
+        node_maps(r);
         const long long nkeys = max_keys;
         r.offsets = (int *)dev_alloc(ctx, sizeof(int) * (nkeys + 1));
         r.block_sums = (int *)dev_alloc(ctx, sizeof(int) * sort_scan_scratch(nkeys));
@@ -610,6 +662,9 @@ MixedStepArgs mixed_args(pic_ctx *ctx, Run &r) {
     a.hist = hist_ref(r);
     a.err = ctx->d_err;
     for (int q = 0; q < 4; ++q) a.key_counts[q] = nullptr;
+    a.use_tma = r.tma ? 1 : 0;
+    a.tmA = r.tmA;
+    a.tmB = r.tmB;
     return a;
 }
 
@@ -811,6 +866,9 @@ void step_run(pic_ctx *ctx, Run &r) {
             a.mode = 0;
             a.hist = hist_ref(r);
             a.err = ctx->d_err;
+            a.use_tma = r.tma ? 1 : 0;
+            a.tmA = r.tmA;
+            a.tmB = r.tmB;
             // when the next step sorts, this push counts its key histogram
             const bool count = r.since_sort + 1 >= r.sort_interval && r.t.lg[0] >= 0;
             prepare_counts(ctx, r);
@@ -1404,6 +1462,7 @@ void apply_tuning(pic_ctx *ctx, const int T[3], int K) {
         const bool same = t.T[0] == r.t.T[0] && t.T[1] == r.t.T[1] && t.T[2] == r.t.T[2];
         r.t = t;
         r.sort_interval = K;
+        node_maps(r);
         if (!same) {
             r.sorted = false;
             for (int q = 0; q < r.d.nspecies; ++q) {

@@ -21,6 +21,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap (the descriptor type only; encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 namespace pic {
@@ -154,6 +155,11 @@ struct MixedStepArgs {
     // when non-null: per species, the push adds to key_counts[s][key] the number of
     // particles whose new cell has that sort key (the next sort's histogram)
     int *key_counts[4];
+    // TMA descriptors of the node-field arrays nfA (4 floats per node) and nfB
+    // (2 floats per node) with a box of one tile + halo; use_tma = 0 when the
+    // geometry breaks a TMA alignment rule (odd tile width or odd padded x extent)
+    int use_tma;
+    CUtensorMap tmA, tmB;
 };
 void launch_push_mixed(const MixedStepArgs &a, cudaStream_t s);
 // persistent launch over the tiles of many runs (same ndim and tile shape)

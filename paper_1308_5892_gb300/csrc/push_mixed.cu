@@ -232,6 +232,45 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// mbarrier and TMA tensor copies (node-field staging).
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for phase `parity` of the barrier; false if it did not complete
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load(int ndim, uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                         uint32_t bar) {
+    if (ndim == 3)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];\n" ::"r"(dst), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+            : "memory");
+    else
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];\n" ::"r"(dst), "l"(map), "r"(c0), "r"(c1), "r"(bar)
+            : "memory");
+}
+
 constexpr int kQueue = 64;      // per-warp ring of waiting pieces (at most 63 wait at any time)
 constexpr int kStages = 3;      // per-warp particle prefetch ring
 // words of one particle in a stage: cell, NDIM offsets, 3 momenta
@@ -340,9 +379,15 @@ __device__ __forceinline__ void drain_one(const int *q_base, const float *q_d, c
 }
 
 // All species of one tile of one run (the body of both launch forms below).
+// Offset of the nfB stage after the nfA stage of `nodes` nodes (TMA destinations are 128-byte aligned).
+__host__ __device__ inline size_t node_b_offset(int nodes) { return ((size_t)nodes * 16 + 127) & ~size_t(127); }
+
+// tmaps: the arguments' copy whose TMA descriptors are in parameter or global
+// memory (the multi-run kernel stages its arguments in shared memory).
 template <int NDIM, int THREADS, bool WALLS, bool HIST>
-__device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile) {
-    extern __shared__ float4 smem4[];
+__device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile, const MixedStepArgs *tmaps) {
+    extern __shared__ __align__(128) float4 smem4[];
+    __shared__ __align__(8) unsigned long long tma_bar;
     constexpr int WARPS = THREADS / 32;
     constexpr int NW = words_per_particle<NDIM>();
     const Geom &g = a.g;
@@ -358,24 +403,39 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
     tc.H = T.H; tc.T0 = T.T[0]; tc.T1 = T.T[1]; tc.T2 = T.T[2];
     const int nodes = tc.nodes;
     float4 *nA = smem4;
-    float2 *nB = reinterpret_cast<float2 *>(smem4 + nodes);
+    float2 *nB = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem4) + node_b_offset(nodes));
     int *Jhi = reinterpret_cast<int *>(nB + nodes);
     int *Jlo = Jhi + 3 * nodes;
     tc.nA = nA; tc.nB = nB; tc.Jhi = Jhi; tc.Jlo = Jlo;
 
-    // Stage node fields of the box [x0-H, x0+T+H) (padded coordinates x0 .. x0+R).
-    for (int q = threadIdx.x; q < nodes; q += THREADS) {
-        const int lx = q % tc.Rx, ly = (q / tc.Rx) % tc.Ry, lz = q / tc.sxy;
-        const int gx = tc.x0 + lx, gy = tc.y0 + ly, gz = tc.z0 + lz;
-        float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 vb = make_float2(0.f, 0.f);
-        if (gx < g.px && gy < g.py && gz < g.pz) {
-            const long long p = ((long long)gz * g.py + gy) * g.px + gx;
-            va = __ldg(a.nfA + p);
-            vb = __ldg(a.nfB + p);
+    // Stage node fields of the box [x0-H, x0+T+H) (padded coordinates x0 .. x0+R):
+    // one TMA tensor copy per array (zeros beyond the padded grid), or coalesced
+    // loads when the geometry breaks a TMA alignment rule.
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&tma_bar);
+    if (a.use_tma) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            // earlier generic accesses to the stage (a previous tile) come before the copies
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_expect_tx(bar, (uint32_t)nodes * 24u);
+            tma_load(NDIM, (uint32_t)__cvta_generic_to_shared(nA), &tmaps->tmA, 4 * tc.x0, tc.y0, tc.z0, bar);
+            tma_load(NDIM, (uint32_t)__cvta_generic_to_shared(nB), &tmaps->tmB, 2 * tc.x0, tc.y0, tc.z0, bar);
         }
-        nA[q] = va;
-        nB[q] = vb;
+    } else {
+        for (int q = threadIdx.x; q < nodes; q += THREADS) {
+            const int lx = q % tc.Rx, ly = (q / tc.Rx) % tc.Ry, lz = q / tc.sxy;
+            const int gx = tc.x0 + lx, gy = tc.y0 + ly, gz = tc.z0 + lz;
+            float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 vb = make_float2(0.f, 0.f);
+            if (gx < g.px && gy < g.py && gz < g.pz) {
+                const long long p = ((long long)gz * g.py + gy) * g.px + gx;
+                va = __ldg(a.nfA + p);
+                vb = __ldg(a.nfB + p);
+            }
+            nA[q] = va;
+            nB[q] = vb;
+        }
     }
     for (int q = threadIdx.x; q < 6 * nodes; q += THREADS) Jhi[q] = 0;   // hi and lo limbs
 
@@ -393,6 +453,11 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
     const uint32_t *stage = reinterpret_cast<const uint32_t *>(wsm + 7 * kQueue);   // [kStages][NW][32]
     const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage) + 4u * lane;
     __syncthreads();
+    if (a.use_tma && !mbar_wait_bounded(bar, 0, 1 << 22)) {
+        // the copy did not land in time: flag it, give it a second bounded wait, go on
+        atomicOr(a.err, ERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0, 1 << 22);
+    }
 
     RegAcc<NDIM> acc;
     acc.q0 = -1;
@@ -556,13 +621,14 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
         atomicAdd(slot + threadIdx.x, t);
     }
     __syncthreads();   // shared memory is reused by the next tile of a persistent CTA
+    if (a.use_tma && threadIdx.x == 0) mbar_inval(bar);
 }
 
 // One CTA per tile of one run; WALLS: conducting walls in x (a separate
 // instantiation keeps their register cost out of the periodic kernel).
 template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
-__global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(MixedStepArgs a) {
-    push_tile<NDIM, THREADS, WALLS, HIST>(a, blockIdx.x);
+__global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(const __grid_constant__ MixedStepArgs a) {
+    push_tile<NDIM, THREADS, WALLS, HIST>(a, blockIdx.x, &a);
 }
 
 // Persistent form for a batch of independent runs of uneven size: resident
@@ -573,7 +639,7 @@ template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedStepArgs *runs, const int *tile_prefix,
                                                                     int nruns, int *counter) {
     __shared__ int item_sh;
-    __shared__ __align__(16) MixedStepArgs args_sh;
+    __shared__ __align__(128) MixedStepArgs args_sh;
     const int total = tile_prefix[nruns];
     for (;;) {
         if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
@@ -589,7 +655,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedS
         int *dst = reinterpret_cast<int *>(&args_sh);
         for (int q = threadIdx.x; q < (int)(sizeof(MixedStepArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
         __syncthreads();
-        push_tile<NDIM, THREADS, WALLS, HIST>(args_sh, item - tile_prefix[lo]);
+        push_tile<NDIM, THREADS, WALLS, HIST>(args_sh, item - tile_prefix[lo], runs + lo);
     }
 }
 
@@ -623,7 +689,7 @@ size_t mixed_smem_bytes(const TileGeom &t, int ndim) {
     const size_t nodes = (size_t)t.R[0] * t.R[1] * (ndim == 3 ? t.R[2] : 1);
     const int warps = (ndim == 3 ? 512 : 256) / 32;
     const size_t wwords = ndim == 3 ? warp_smem_words<3>() : warp_smem_words<2>();
-    return nodes * (sizeof(float4) + sizeof(float2) + 6 * sizeof(int)) + (size_t)warps * wwords * sizeof(int);
+    return node_b_offset((int)nodes) + nodes * (sizeof(float2) + 6 * sizeof(int)) + (size_t)warps * wwords * sizeof(int);
 }
 
 void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
