@@ -29,10 +29,16 @@ template <int NDIM>
 __device__ inline int cell_key(const TileGeom &t, uint32_t c) {
     int i, j, k;
     unpack_cell(NDIM, c, i, j, k);
+    if (t.lg[0] >= 0) return tile_key_pow2(t, i, j, k);   // shifts instead of divisions
     const int ti = i / t.T[0], tj = j / t.T[1], tk = NDIM == 3 ? k / t.T[2] : 0;
     const int li = i - ti * t.T[0], lj = j - tj * t.T[1], lk = NDIM == 3 ? k - tk * t.T[2] : 0;
     const int tile = (tk * t.ntile[1] + tj) * t.ntile[0] + ti;
     return tile * t.cells_per_tile + (lk * t.T[1] + lj) * t.T[0] + li;
+}
+
+// Tile of a key.
+__device__ inline int key_tile(const TileGeom &t, int key) {
+    return t.lg[0] >= 0 ? key >> (t.lg[0] + t.lg[1] + t.lg[2]) : key / t.cells_per_tile;
 }
 
 // Position of cell-sorted rank r inside a tile of n_t particles: every full
@@ -226,7 +232,7 @@ __device__ inline void rank_body(const SortArgs &a, const SrcWalk &w, long long 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             if (key[v] < 0) continue;
-            const int tile = key[v] / a.t.cells_per_tile;
+            const int tile = key_tile(a.t, key[v]);
             const int t0 = __ldg(a.tile_start + tile), t1 = __ldg(a.tile_start + tile + 1);
             const long long dst = (long long)t0 + interleaved_slot(base[v] - t0, t1 - t0);
             if (base[v] >= t0 && base[v] < t1 && dst < a.n) a.perm[dst] = (int)p[v];
@@ -270,7 +276,7 @@ __device__ inline void gather_body(const SpeciesMixed &src, const SpeciesMixed &
                 p[v] = qq < q1 ? __ldg(perm + qq) : -1;
             }
             uint32_t x[4];
-            // an out-of-range entry exists only after a bad key, which the histogram has flagged
+            // an out-of-range entry exists only after a bad key, which the sort has flagged
 #pragma unroll
             for (int v = 0; v < 4; ++v) x[v] = (p[v] >= 0 && p[v] < n) ? __ldg(sa + p[v]) : 0u;
 #pragma unroll
