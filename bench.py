@@ -334,6 +334,13 @@ def _e2e(pic, torch, desc, w, seed, args, barrier):
     return e2e_s, nbytes, nbytes
 
 
+# DRAM bytes (read + written) per particle-step of the 3D push kernel, from one
+# ncu capture of the same kernel and tiling on the 64^3 case (profiles/
+# push_mixed_thermal3d_64.md: 917.4 MB for 16,777,216 particles), scaled to a
+# launch by the particles it processes.  None where no capture exists.
+PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.4e6 / 16777216}
+
+
 def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1):
     m = results["mixed"]
     value_rank = npart * m["steps"] / (m["ms"] * 1e6)
@@ -356,7 +363,10 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                                               "unit": "particle-steps/ns", "ms_per_step": f64["ms"] / f64["steps"],
                                               "steps": f64["steps"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_push_mixed (gather+push+deposit, both species)",
+                         "traffic": (PUSH_TRAFFIC_B_PER_PARTICLE.get(w.get("ndim"), 0.0) * npart
+                                     if w.get("ndim") in PUSH_TRAFFIC_B_PER_PARTICLE and nruns == 1 else None),
+                         "traffic_source": "ncu dram bytes of the same kernel at 64^3, scaled by particles",
+                         "kernel": "k_push_mixed (gather+push+deposit, both species)",
                          "peak_kind": peak_kind, "push_ms_per_step": push_launch_ms,
                          "field_ms_per_step": m["field_ms"] / m["steps"], "sort_ms_total": m["sort_ms"],
                          "sort_interval": m["tuning"]["sort_interval"],
