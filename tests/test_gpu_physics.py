@@ -176,3 +176,48 @@ def test_thermal_plasma_energy_drift_scales_as_one_over_rho_sp_in_both_paths():
     for name in ("fp64", "mixed"):
         ratio = rates[name, 8] / rates[name, 32]
         assert 2.5 <= ratio <= 6.0, (name, ratio)
+
+
+def _mj_cutoff_factor(theta):
+    """<gamma^-1 (1 - beta^2 / 3)> over a Maxwell-Juttner distribution at rest,
+    by quadrature in u = gamma beta: weight u^2 exp(-gamma / theta)."""
+    from scipy import integrate
+    w = lambda u: u * u * np.exp(-(np.sqrt(1 + u * u) - 1) / theta)
+    f = lambda u: w(u) / np.sqrt(1 + u * u) * (1 - (u * u / (1 + u * u)) / 3)
+    top = integrate.quad(f, 0, np.inf, limit=400)[0]
+    bot = integrate.quad(w, 0, np.inf, limit=400)[0]
+    return top / bot
+
+
+def test_thermal_plasma_k0_spectrum_peaks_at_the_relativistic_cutoff():
+    """Sect. 3.1: the k = 0 electric field of a thermal pair plasma oscillates
+    at the plasma cutoff, omega_cut^2 = omega_P^2 <gamma^-1 (1 - beta^2/3)> with
+    omega_P^2 = 2 omega_pe^2 for pairs (relativistic correction of the paper's
+    omega_P).  Configuration 1: 64^2, theta = 0.1, n_x = theta^-1/2 (dx = Debye
+    length), 16 ppc per species, dt = 0.5, run over 60 plasma periods; the peak
+    of |FFT_t <e_x>|^2 must fall within 2 % of omega_cut in both paths, and the
+    two paths within two frequency bins of each other (the peak of a noise-driven
+    spectrum moves by a bin between realisations)."""
+    theta, ppc, nsteps, dt = 0.1, 16, 2400, 0.5
+    n_x = theta ** -0.5
+    n = ppc * 64 * 64
+    d = pic.run_desc(2, 64, 64, 1, n_x, 2.0 * ppc, dt, [(-1.0, 1.0, n), (1.0, 1.0, n)])
+    omega_cut = np.sqrt(2.0) / n_x * np.sqrt(_mj_cutoff_factor(theta))
+    peaks = {}
+    for name, prec in (("fp64", pic.PIC_FP64), ("mixed", pic.PIC_MIXED)):
+        with pic.Context([d], precision=prec) as ctx:
+            ctx.load_maxwell_juttner(0, 0, ppc, theta, seed=1)
+            ctx.load_maxwell_juttner(0, 1, ppc, theta, colocate_with=0, seed=2)
+            ex = np.zeros(nsteps)
+            for k in range(nsteps):
+                ctx.step(1)
+                f, _, _ = ctx.get_state(0, fields_only=True)
+                ex[k] = f[0].mean()
+        spec = np.abs(np.fft.rfft((ex - ex.mean()) * np.hanning(nsteps))) ** 2
+        omega = 2 * np.pi * np.fft.rfftfreq(nsteps, dt)
+        peaks[name] = omega[1 + np.argmax(spec[1:])]
+    dw = 2 * np.pi / (nsteps * dt)
+    print("k=0 peak: fp64 %.4f mixed %.4f theory %.4f (bin %.4f)" % (peaks["fp64"], peaks["mixed"], omega_cut, dw))
+    for name, w in peaks.items():
+        assert abs(w / omega_cut - 1) <= 0.02, (name, w, omega_cut)
+    assert abs(peaks["mixed"] - peaks["fp64"]) <= 2 * dw + 1e-12
