@@ -397,3 +397,34 @@ def test_field_energy_units():
     st.e[0][:] = 2.0
     en = oracle.energies(st)
     assert np.isclose(en["field_e"][0], 16 * 0.5 * 4.0 / (2.0 / (9.0 * 10.0)))
+
+
+def test_thermal_plasma_k0_oscillation_is_at_the_relativistic_cutoff():
+    """Sect. 3.1: the k = 0 electric field of a thermal pair plasma oscillates
+    at omega_cut = omega_P <gamma^-1 (1 - beta^2/3)>^(1/2), omega_P^2 = 2/n_x^2
+    for pairs (n_x cells per c/omega_pe).  A small box (16^2, theta = 0.1,
+    dx = lambda_D, 16 ppc per species) over 60 plasma periods: the peak of the
+    power spectrum of the box-mean e_x lies within 3 % of the cutoff (the
+    frequency bins are 1.3 % of it)."""
+    from scipy import integrate
+    from oracle import mj
+    theta, ppc, nsteps, dt, nx = 0.1, 16, 2400, 0.5, 16
+    n_x = theta ** -0.5
+    n = ppc * nx * nx
+    st = oracle.State.empty(2, nx, nx, 1, dt, n_x, 2.0 * ppc)
+    pos, u0 = mj.load(5, 0, n, theta, (0.0, 0.0, 0.0), 2, nx, nx, 1)
+    _, u1 = mj.load(6, 1, n, theta, (0.0, 0.0, 0.0), 2, nx, nx, 1)
+    st.species.append(oracle.Species(pos, u0, -1.0, 1.0))
+    st.species.append(oracle.Species(pos.copy(), u1, 1.0, 1.0))
+    ex = np.zeros(nsteps)
+    for k in range(nsteps):
+        oracle.step(st)
+        ex[k] = st.e[0].mean()
+    spec = np.abs(np.fft.rfft((ex - ex.mean()) * np.hanning(nsteps))) ** 2
+    omega = 2 * np.pi * np.fft.rfftfreq(nsteps, dt)
+    peak = omega[1 + np.argmax(spec[1:])]
+    w = lambda uu: uu * uu * np.exp(-(np.sqrt(1 + uu * uu) - 1) / theta)
+    f = lambda uu: w(uu) / np.sqrt(1 + uu * uu) * (1 - (uu * uu / (1 + uu * uu)) / 3)
+    factor = integrate.quad(f, 0, np.inf, limit=400)[0] / integrate.quad(w, 0, np.inf, limit=400)[0]
+    omega_cut = np.sqrt(2.0) / n_x * np.sqrt(factor)
+    assert abs(peak / omega_cut - 1) <= 0.03, (peak, omega_cut)
