@@ -160,8 +160,35 @@ def _time_oracle_sample(w, steps, seed):
     return npart * steps / (dt * 1e9), dt, npart, steps, sw
 
 
+def rank_env():
+    """(rank, world size, local rank) of this process, as torch.distributed.run sets them."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def replica_seed(rank):
+    """Seed of the replica on `rank`: every GPU advances its own independent run."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time: the job is done when every replica is."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(npart_rank, steps, ms_max, world):
+    """Whole-job particle-steps/ns: each of `world` replicas advances npart_rank
+    particles (weak scaling) and the job takes the slowest rank's ms_max."""
+    return npart_rank * steps * world / (ms_max * 1e6)
+
+
 def run_reference(args, w):
-    rank = int(os.environ.get("RANK", "0"))
+    rank, _, _ = rank_env()
     if rank != 0:
         return 0
     times = []
@@ -189,9 +216,7 @@ def run_ours(args, w):
     import torch
     import paper_1308_5892_gb300 as pic
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -203,7 +228,7 @@ def run_ours(args, w):
             dist.barrier()
         torch.cuda.synchronize()
 
-    seed = 2 + 1000 * rank
+    seed = replica_seed(rank)
     if w.get("ensemble"):
         members = ensemble_members(w["ensemble"])
         descs = []
@@ -287,10 +312,7 @@ def run_ours(args, w):
         field_ms, field_n = ctx.kernel_time(pic.PIC_KERNEL_FIELD)
         sort_ms, sort_n = ctx.kernel_time(pic.PIC_KERNEL_SORT, reset=True)
         diag = ctx.diagnostics(0)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         results[name] = dict(ms=ms, ms_direct=ms_t, steps=steps, push_ms=push_ms, push_n=push_n, field_ms=field_ms,
                              sort_ms=sort_ms, counters=cnt, clocks=clk, diag=diag,
                              tuning=dict(ctx.tuning(), autotune=tuned) if prec == pic.PIC_MIXED else None)
@@ -304,6 +326,7 @@ def run_ours(args, w):
     h2d = d2h = 0
     if not args.no_e2e and members is None:
         e2e_s, h2d, d2h = _e2e(pic, torch, descs[0], w, seed, args, barrier)
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     if args.no_fp64:
         results["fp64"] = None
     return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, len(descs))
@@ -343,8 +366,7 @@ PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.4e6 / 16777216}
 
 def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1):
     m = results["mixed"]
-    value_rank = npart * m["steps"] / (m["ms"] * 1e6)
-    value = value_rank * world
+    value = job_value(npart, m["steps"], m["ms"], world)
     f64 = results["fp64"]
     peak, peak_kind = _peaks()
     push_launch_ms = m["push_ms"] / max(m["push_n"], 1)
