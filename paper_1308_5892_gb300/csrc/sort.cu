@@ -249,7 +249,7 @@ __device__ inline void rank_body(const SortArgs &a, const SrcWalk &w, long long 
 // grid-stride loop over the whole array spreads the resident threads over all
 // of it and fetches each 32-byte sector many times for its 4 used bytes.)
 constexpr int kGatherThreads = 256;
-constexpr int kGatherChunk = 8192;
+constexpr int kGatherChunk = 4096;
 
 template <int NDIM>
 __device__ inline void gather_body(const SpeciesMixed &src, const SpeciesMixed &dst, long long n, const int *perm,
