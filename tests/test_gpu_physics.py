@@ -221,3 +221,45 @@ def test_thermal_plasma_k0_spectrum_peaks_at_the_relativistic_cutoff():
     for name, w in peaks.items():
         assert abs(w / omega_cut - 1) <= 0.02, (name, w, omega_cut)
     assert abs(peaks["mixed"] - peaks["fp64"]) <= 2 * dw + 1e-12
+
+
+def test_harris_sheet_tearing_grows_at_the_same_rate_in_both_paths():
+    """Config 5 (Sect. 3.4, App. C): a relativistic pair Harris sheet between
+    conducting walls, Theta = 1 with the Table tearing relations (omega_ce /
+    omega_pe = 1.82, Gamma U = 0.68, L = 1.62 d_e), loaded by the library's
+    Harris profile with drifting Maxwell-Juttner beams; the current is along the
+    ignorable z, B_y(x) = B0 tanh((x - x0)/L).  The tearing mode (k along y)
+    makes b_x grow; its energy must grow at the same rate in the FP64 and the
+    mixed path (within 10 %), over a linear phase of at least two decades."""
+    theta, GU, wce, l_over_de = 1.0, 0.68, 1.82, 1.62
+    n_x, ppc, nx, ny, dt, nsteps = 4.0, 16, 128, 256, 0.5, 1600
+    L, x0 = l_over_de * n_x, nx / 2.0
+    beta = GU / np.sqrt(1.0 + GU * GU)
+    b0 = wce / n_x                                    # omega_ce in units of c / X0 with X0 = d_e / n_x
+    cap = int(ppc * 2.2 * L * ny) + 1024
+    d = pic.run_desc(2, nx, ny, 1, n_x, 2.0 * ppc, dt, [(-1.0, 1.0, cap), (1.0, 1.0, cap)], bc=(1, 0, 0))
+    rates = {}
+    for name, prec in (("fp64", pic.PIC_FP64), ("mixed", pic.PIC_MIXED)):
+        with pic.Context([d], precision=prec) as ctx:
+            # electrons drift along -z, positrons along +z: J_z > 0 at the centre, dB_y/dx = J_z
+            ctx.load_maxwell_juttner(0, 0, ppc, theta, (0.0, 0.0, -beta), profile=pic.PIC_PROFILE_HARRIS,
+                                     profile_params=(L, x0), seed=41)
+            ctx.load_maxwell_juttner(0, 1, ppc, theta, (0.0, 0.0, beta), profile=pic.PIC_PROFILE_HARRIS,
+                                     profile_params=(L, x0), colocate_with=0, seed=42)
+            f, p, _ = ctx.get_state(0)
+            i = np.arange(nx)
+            f[4, 0, :, :] = b0 * np.tanh((i[None, :] + 0.5 - x0) / L)    # b_y at (i + 1/2, j)
+            ctx.set_state(0, f, p)
+            ebx = np.zeros(nsteps)
+            for k in range(nsteps):
+                ctx.step(1)
+                g, _, _ = ctx.get_state(0, fields_only=True)
+                ebx[k] = (g[3] ** 2).sum()
+        rates[name] = _linear_phase_rate(ebx, dt)
+        print("tearing %s: E_bx from %.3e to %.3e, growth rate %s" % (name, ebx[30], ebx.max(), rates[name]))
+    T_pe = 2 * np.pi * n_x
+    for name, r in rates.items():
+        if r:
+            print("tearing %s: tau = %.2f T_pe (paper: 2.5 T_pe at n_x = 15)" % (name, 1.0 / r / T_pe))
+    assert rates["fp64"] and rates["mixed"], rates
+    assert abs(rates["mixed"] / rates["fp64"] - 1) <= 0.10, rates
