@@ -263,3 +263,29 @@ def test_harris_sheet_tearing_grows_at_the_same_rate_in_both_paths():
             print("tearing %s: tau = %.2f T_pe (paper: 2.5 T_pe at n_x = 15)" % (name, 1.0 / r / T_pe))
     assert rates["fp64"] and rates["mixed"], rates
     assert abs(rates["mixed"] / rates["fp64"] - 1) <= 0.10, rates
+
+
+def test_ensemble_field_fluctuation_level_scales_as_one_over_ppc():
+    """Config 4 (Sect. 5.3): in thermal equilibrium each field mode holds an
+    energy of order the temperature, so the field-fluctuation level, the field
+    energy over the kinetic energy, falls as 1 / (particles per cell).  Five
+    runs of one batched ensemble (64^2, theta = 0.1, n_x = theta^-1/2, 4 to 64
+    ppc per species), levels averaged over steps 100-300; the log-log slope
+    against ppc must be -1 within 0.25 (the paper pins the scaling, not the
+    constant)."""
+    theta, n_x = 0.1, 0.1 ** -0.5
+    ppcs = [4, 8, 16, 32, 64]
+    descs = [pic.run_desc(2, 64, 64, 1, n_x, 2.0 * ppc, 0.5,
+                          [(-1.0, 1.0, ppc * 4096), (1.0, 1.0, ppc * 4096)]) for ppc in ppcs]
+    with pic.Context(descs, precision=pic.PIC_MIXED) as ctx:
+        for r, ppc in enumerate(ppcs):
+            ctx.load_maxwell_juttner(r, 0, ppc, theta, seed=50 + 2 * r)
+            ctx.load_maxwell_juttner(r, 1, ppc, theta, colocate_with=0, seed=51 + 2 * r)
+        ctx.step(300)
+        level = []
+        for r in range(len(ppcs)):
+            h = ctx.energy_history(r)
+            level.append(((h[100:, 1] + h[100:, 2]) / h[100:, 0]).mean())
+    slope = np.polyfit(np.log(ppcs), np.log(level), 1)[0]
+    print("fluctuation level by ppc:", dict(zip(ppcs, np.round(level, 6))), "slope %.3f" % slope)
+    assert abs(slope + 1.0) <= 0.25, slope
