@@ -1,5 +1,7 @@
 // capi.cu -- host runtime behind the C ABI of include/pic.h: context and device
-// memory, state transfer, step orchestration, diagnostics.
+// memory, state transfer (values validated on the device while converted),
+// step orchestration for one run or a batched ensemble, CUDA-graph capture and
+// replay of the mixed step, the autotuner, diagnostics, the learned sampler.
 //
 // One step of one run (main loop of App. A.3.1), state e^t, b^{t-dt/2}, x^t, u^{t-dt/2}:
 //   [re-sort particles by tile when due]                    (mixed path)

@@ -4,13 +4,15 @@
 // so particles end up grouped by tile and, inside a tile, by cell; the cell
 // order inside a tile is then stored block-transposed (interleaved_slot).  The sort
 // is out of place (src -> dst, the caller swaps the buffers): histogram of the
-// keys, exclusive scan, a rank pass whose per-key cursors are advanced with
-// warp-aggregated atomics (lanes of a warp that share a key take consecutive
-// slots with one atomic) and which writes only the 4-byte inverse permutation,
-// then a gather pass that writes every particle array in destination order
-// (coalesced stores; scattered partial-sector stores of the full particle
-// state cost several times its size in DRAM traffic).  The tile offsets are
-// read from the scanned counts.
+// keys (unless the preceding push counted it), exclusive scan, a rank pass
+// whose per-key cursors are advanced with warp-aggregated atomics (lanes of a
+// warp that share a key take consecutive slots with one atomic) and which
+// writes only the 4-byte inverse permutation, then a gather pass that writes
+// every particle array in destination order (coalesced stores; scattered
+// partial-sector stores of the full particle state cost several times its size
+// in DRAM traffic).  The tile offsets are read from the scanned counts, and
+// the counts are left zeroed for the next push to count into.  Every phase also
+// has a batched form that sorts one species of many runs in one launch.
 //
 // Roofline: HBM bound; per particle 4 B (histogram) + 8 B (rank) +
 // 4 + 2 x (24..28 + 4) B (gather) plus per key 3 x 4 B.  Particle counts are
