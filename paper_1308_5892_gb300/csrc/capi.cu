@@ -115,6 +115,10 @@ struct pic_ctx {
     bool capturing = false;
     char *gstage = nullptr;            // pinned per-step copies of the argument tables (ensemble)
     size_t gstage_stride = 0, gstage_bytes = 0;
+    // state uploads: host-to-device copies on a stream of their own, overlapped
+    // with the conversion kernels through two halves of the staging buffer
+    cudaStream_t io_stream = nullptr;
+    cudaEvent_t io_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // start, loaded/filled[2], consumed/copied[2]
     std::vector<FieldRunF> h_fe, h_fp;
     // PIC_FLAG_TIMING: event pairs per kernel class, resolved in pic_kernel_time
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[3];
@@ -572,6 +576,14 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
 pic_status check_run(pic_ctx *ctx, int run) {
     if (!ctx) return PIC_EINVAL;
     if (run < 0 || run >= (int)ctx->runs.size()) return fail(ctx, PIC_EINVAL, "run index %d out of range", run);
+    return PIC_OK;
+}
+
+// The transfer stream and its events, created on first use.
+pic_status io_ready(pic_ctx *ctx) {
+    if (!ctx->io_stream) CK(cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking));
+    for (auto &e : ctx->io_ev)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return PIC_OK;
 }
 
@@ -1136,6 +1148,9 @@ void pic_destroy(pic_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->io_stream) cudaStreamSynchronize(ctx->io_stream), cudaStreamDestroy(ctx->io_stream);
+    for (auto e : ctx->io_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->gstage) cudaFreeHost(ctx->gstage);
     for (int k = 0; k < 3; ++k)
         for (auto &pr : ctx->ev_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -1168,6 +1183,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
         pic_status st0 = read_err(ctx);
         (void)st0;
     }
+    if (ctx->precision == PIC_MIXED && (st = io_ready(ctx)) != PIC_OK) return st;
     double *stg = (double *)ctx->staging;
     const size_t rs = real_size(ctx);
     for (int c = 0; c < 6; ++c) {
@@ -1197,15 +1213,30 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
             S.cur = 0;
             S.tiled = false;
             S.counted = false;
-            const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
-            for (int64_t a0 = 0; a0 < n; a0 += chunk) {
+            // chunk c is copied into half c % 2 on the transfer stream while the
+            // previous chunk is converted on the context stream
+            const size_t half = (ctx->staging_bytes / 2) & ~size_t(255);
+            double *hb[2] = {stg, (double *)((char *)stg + half)};
+            const int64_t chunk = std::max<int64_t>(1, (int64_t)(half / (6 * sizeof(double))));
+            cudaStream_t io = ctx->io_stream;
+            CK(cudaEventRecord(ctx->io_ev[0], sm));
+            CK(cudaStreamWaitEvent(io, ctx->io_ev[0], 0));
+            bool used[2] = {false, false};
+            int c = 0;
+            for (int64_t a0 = 0; a0 < n; a0 += chunk, ++c) {
+                const int b = c & 1;
                 const int64_t m = std::min(chunk, n - a0);
+                if (used[b]) CK(cudaStreamWaitEvent(io, ctx->io_ev[3 + b], 0));   // its last reader is done
                 for (int a = 0; a < 6; ++a) {
                     if (a == 2 && g.ndim == 2) continue;
-                    CK(cudaMemcpyAsync(stg + a * m, P + a * n + a0, sizeof(double) * m, cudaMemcpyHostToDevice, sm));
+                    CK(cudaMemcpyAsync(hb[b] + a * m, P + a * n + a0, sizeof(double) * m, cudaMemcpyHostToDevice, io));
                 }
-                k_upload_mixed<<<nblk(m), 256, 0, sm>>>(g, stg, m, a0, S.mb[0], ctx->d_err);
+                CK(cudaEventRecord(ctx->io_ev[1 + b], io));
+                CK(cudaStreamWaitEvent(sm, ctx->io_ev[1 + b], 0));
+                k_upload_mixed<<<nblk(m), 256, 0, sm>>>(g, hb[b], m, a0, S.mb[0], ctx->d_err);
                 CK(cudaGetLastError());
+                CK(cudaEventRecord(ctx->io_ev[3 + b], sm));
+                used[b] = true;
             }
         }
     }
@@ -1253,6 +1284,8 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
             }
             if (g.ndim == 2) std::memset(P + 2 * n, 0, sizeof(double) * n);
         } else {
+            // conversion and copy in turn on the context stream (a copy stream of
+            // its own measured slower here than this serial form)
             const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
             for (int64_t a0 = 0; a0 < n; a0 += chunk) {
                 const int64_t m = std::min(chunk, n - a0);
