@@ -292,7 +292,7 @@ __global__ void k_upload_mixed(Geom g, const double *st, long long m, long long 
 // inverse map id -> storage index, then gather of the requested ids
 __global__ void k_id_index(const int32_t *id, long long n, int *inv) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
-        inv[id[p]] = (int)p;
+        if ((unsigned long long)id[p] < (unsigned long long)n) inv[id[p]] = (int)p;   // ids are 0 .. n-1
 }
 
 __global__ void k_pick_mixed(Geom g, SpeciesMixed s, const int *inv, const long long *ids, long long m, double *st) {
@@ -319,11 +319,11 @@ __global__ void k_pick64(Species64 s, const long long *ids, long long m, int ndi
     }
 }
 
-__global__ void k_download_mixed(Geom g, SpeciesMixed s, long long n, long long a, long long m, double *st) {
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const long long id = s.id[p];
-        if (id < a || id >= a + m) continue;
-        const long long q = id - a;
+// Download of ids [a, a+m) through the id -> storage index map inv: coalesced
+// staging writes, one pass over the chunk's own particles.
+__global__ void k_download_by_id(Geom g, SpeciesMixed s, const int *inv, long long a, long long m, double *st) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        const int p = inv[a + q];
         int i, j, k;
         unpack_cell(g.ndim, s.cell[p], i, j, k);
         st[q] = (double)i + (double)s.off[0][p];
@@ -1285,11 +1285,13 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
             if (g.ndim == 2) std::memset(P + 2 * n, 0, sizeof(double) * n);
         } else {
             // conversion and copy in turn on the context stream (a copy stream of
-            // its own measured slower here than this serial form)
+            // its own measured slower here than this serial form); the id -> storage
+            // index map lets each chunk touch only its own particles
+            k_id_index<<<nblk(n), 256, 0, sm>>>(S.mb[S.cur].id, n, r.perm);
             const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
             for (int64_t a0 = 0; a0 < n; a0 += chunk) {
                 const int64_t m = std::min(chunk, n - a0);
-                k_download_mixed<<<nblk(n), 256, 0, sm>>>(g, S.mb[S.cur], n, a0, m, stg);
+                k_download_by_id<<<nblk(m), 256, 0, sm>>>(g, S.mb[S.cur], r.perm, a0, m, stg);
                 CK(cudaGetLastError());
                 for (int a = 0; a < 6; ++a)
                     CK(cudaMemcpyAsync(P + a * n + a0, stg + a * m, sizeof(double) * m, cudaMemcpyDeviceToHost, sm));
