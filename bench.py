@@ -336,8 +336,10 @@ def _e2e(pic, torch, desc, w, seed, args, barrier):
     """End to end through the C ABI with host buffers: the timed region uploads
     the whole state from pinned host memory, runs the steps and reads the whole
     state back into pinned host memory."""
-    ctx = pic.Context([desc], precision=pic.PIC_MIXED)
+    ctx = pic.Context([desc], precision=pic.PIC_MIXED, tile=tuple(args.tile), sort_interval=args.sort_interval)
     _load(ctx, w, seed)
+    if not args.no_autotune and args.tile == (0, 0, 0) and args.sort_interval == 0:
+        ctx.autotune(max_steps=args.autotune_steps)   # the process-wide cache answers for this workload
     fields, parts, _ = ctx.get_state(0)
     pin_f = torch.from_numpy(fields).pin_memory().numpy()
     pin_p = [torch.from_numpy(p).pin_memory().numpy() for p in parts]

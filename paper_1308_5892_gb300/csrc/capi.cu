@@ -405,7 +405,7 @@ std::vector<std::vector<int>> tile_candidates(int ndim) {
     if (ndim == 2) return {{16, 16, 1}, {32, 16, 1}, {32, 32, 1}, {16, 8, 1}};
     return {{8, 8, 8}, {8, 8, 4}, {16, 8, 4}};
 }
-std::vector<int> sort_candidates(int ndim) { return ndim == 2 ? std::vector<int>{8, 4, 16} : std::vector<int>{2, 3, 1, 4}; }
+std::vector<int> sort_candidates(int ndim) { return ndim == 2 ? std::vector<int>{8, 4, 16} : std::vector<int>{3, 2, 1, 4}; }
 
 void choose_tiles(Run &r, const pic_opts *o, int &max_tiles, long long &max_keys) {
     const pic_run_desc &d = r.d;
