@@ -34,7 +34,8 @@ _lib = None
 
 class _Grid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
-                ("nz", ctypes.c_int), ("dt", ctypes.c_double), ("bc_x", ctypes.c_int)]
+                ("nz", ctypes.c_int), ("dt", ctypes.c_double), ("bc_x", ctypes.c_int),
+                ("smooth_passes", ctypes.c_int)]
 
 
 class _Species(ctypes.Structure):
@@ -64,6 +65,7 @@ def lib():
             "orc_deposit": ([G, P, i64, P, P, d], None),
             "orc_rho": ([G, i64, P, d, P], None),
             "orc_div_e": ([G, P, P], None),
+            "orc_smooth": ([G, P, ctypes.c_int, ctypes.c_int], None),
             "orc_step": ([G, P, P, P, ctypes.c_int, S], None),
             "orc_run": ([G, P, P, P, ctypes.c_int, S, ctypes.c_int], None),
             "orc_stagger_back": ([G, P, P, ctypes.c_int, S], None),
@@ -113,21 +115,22 @@ class State:
     b: np.ndarray
     species: List[Species] = field(default_factory=list)
     bc_x: int = BC_PERIODIC
+    smooth_passes: int = 0   # current smoothing passes per step (App. A.3.4), periodic grids only
 
     @classmethod
-    def empty(cls, ndim, nx, ny, nz, dt, n_x, rho_sp0, bc_x=BC_PERIODIC):
+    def empty(cls, ndim, nx, ny, nz, dt, n_x, rho_sp0, bc_x=BC_PERIODIC, smooth_passes=0):
         if ndim == 2:
             nz = 1
         z = np.zeros((3, nz, ny, nx))
-        return cls(ndim, nx, ny, nz, dt, n_x, rho_sp0, z.copy(), z.copy(), [], bc_x)
+        return cls(ndim, nx, ny, nz, dt, n_x, rho_sp0, z.copy(), z.copy(), [], bc_x, smooth_passes)
 
     def copy(self):
         sp = [Species(s.pos.copy(), s.u.copy(), s.q_over_e, s.m_over_me) for s in self.species]
         return State(self.ndim, self.nx, self.ny, self.nz, self.dt, self.n_x, self.rho_sp0,
-                     self.e.copy(), self.b.copy(), sp, self.bc_x)
+                     self.e.copy(), self.b.copy(), sp, self.bc_x, self.smooth_passes)
 
     def grid(self):
-        return _Grid(self.ndim, self.nx, self.ny, self.nz, self.dt, self.bc_x)
+        return _Grid(self.ndim, self.nx, self.ny, self.nz, self.dt, self.bc_x, self.smooth_passes)
 
     def alpha(self, s):
         return alpha_of(self.species[s].q_over_e, self.n_x, self.rho_sp0)
@@ -231,9 +234,24 @@ def div_e(state: State):
     return out
 
 
+def smooth(state: State, a, passes=1):
+    """The current smoothing of App. A.3.4 applied ``passes`` times to every
+    plane of ``a`` (shape (nz, ny, nx) or (m, nz, ny, nx)); returns a new array."""
+    out = np.array(a, dtype=np.float64, order="C", copy=True)
+    nplanes = 1 if out.ndim == 3 else out.shape[0]
+    g = state.grid()
+    lib().orc_smooth(ctypes.byref(g), _ptr(out), nplanes, passes)
+    return out
+
+
 def gauss_residual(state: State):
-    """(max |div e - rho~|, max over species of max |rho~_s|)."""
-    r = div_e(state) - rho(state)
+    """(max |div e - S^P rho~|, max over species of max |rho~_s|), S^P the
+    current smoothing of the run (identity when it is off): smoothing the
+    current by S conserves div e - S rho~ instead of div e - rho~."""
+    rho_all = rho(state)
+    if state.smooth_passes > 0:
+        rho_all = smooth(state, rho_all, state.smooth_passes)
+    r = div_e(state) - rho_all
     rmax = max((np.abs(rho(state, s)).max() for s in range(len(state.species))), default=0.0)
     return float(np.abs(r).max()), float(rmax)
 

@@ -33,6 +33,9 @@
  *    e_y = e_z = b_x = 0 on the wall, staggered values outside the domain
  *    read as zero in the gather, particles are reflected specularly and the
  *    deposit follows the path to the wall and the mirrored remainder.
+ *  - Current smoothing (App. A.3.4) acts on the periodic current, i.e. after
+ *    the images of a periodic grid have been summed; one call of the paper's
+ *    step 10 is one pass.  It is defined here for periodic axes only.
  */
 #include <math.h>
 #include <stdint.h>
@@ -47,6 +50,7 @@ typedef struct {
     int nx, ny, nz;    /* cells; nz = 1 when ndim = 2 */
     double dt;         /* time step in X0/c */
     int bc_x;          /* ORC_BC_PERIODIC or ORC_BC_CONDUCTOR (walls at x = 0, nx) */
+    int smooth_passes; /* current smoothing of App. A.3.4 applied this many times (0: off; periodic grids) */
 } orc_grid;
 
 typedef struct {
@@ -58,7 +62,7 @@ typedef struct {
     double alpha;      /* current coupling alpha_s = 2 sgn(q_s) / (n_x^2 rho_sp0), Eq. alpha */
 } orc_species;
 
-int orc_abi_version(void) { return 3; }
+int orc_abi_version(void) { return 4; }
 
 static long wrapi(long i, long n) { long r = i % n; return r < 0 ? r + n : r; }
 
@@ -445,6 +449,42 @@ void orc_div_e(const orc_grid *g, const double *e, double *div) {
             }
 }
 
+/* Current smoothing (App. A.3.4, main-loop step 10), applied `passes` times
+ * to each of `nplanes` grid planes.  One pass replaces the value of cell
+ * (i,j,k) by the weighted mean of its 3x3x3 neighbourhood: weight 1 for the
+ * cell itself, 1/2 for the six cells that differ in one index, 1/4 for the
+ * twelve that differ in two and 1/8 for the eight that differ in three, the
+ * sum divided by the total weight.  Neighbour indices wrap periodically; in
+ * 2D3V (nz = 1) the z neighbours are the cell itself, which is the same
+ * smoothing of a z-independent field.  Every pass reads a copy of the
+ * previous values, so the result does not depend on the sweep order. */
+void orc_smooth(const orc_grid *g, double *a, int nplanes, int passes) {
+    long nc = ncell(g);
+    double *prev = (double *)malloc(sizeof(double) * nc);
+    for (int q = 0; q < nplanes; ++q) {
+        double *v = a + q * nc;
+        for (int pass = 0; pass < passes; ++pass) {
+            memcpy(prev, v, sizeof(double) * nc);
+            for (long k = 0; k < g->nz; ++k)
+                for (long j = 0; j < g->ny; ++j)
+                    for (long i = 0; i < g->nx; ++i) {
+                        double sum = 0.0, wsum = 0.0;
+                        for (int dk = -1; dk <= 1; ++dk)
+                            for (int dj = -1; dj <= 1; ++dj)
+                                for (int di = -1; di <= 1; ++di) {
+                                    int shifted = (di != 0) + (dj != 0) + (dk != 0);
+                                    double w = 1.0;
+                                    for (int m = 0; m < shifted; ++m) w *= 0.5;
+                                    sum += w * prev[cidx(g, i + di, j + dj, k + dk)];
+                                    wsum += w;
+                                }
+                        v[cidx(g, i, j, k)] = sum / wsum;
+                    }
+        }
+    }
+    free(prev);
+}
+
 /* ------------------------------------------------------------ main loop */
 
 /* One step of the main loop of App. A.3.1.  State on entry: x^t, u^{t-dt/2},
@@ -458,10 +498,11 @@ void orc_div_e(const orc_grid *g, const double *e, double *div) {
  *  7  boundary for e
  *  8  boundary for particles
  *  9  currents from the displacement x^t -> x^{t+dt}
- * 10  filtering: off
+ * 10  smoothing of the currents, g->smooth_passes times (App. A.3.4)
  * 11  boundary for the currents (periodic indices fold them)
  * 12  e += currents, e boundary again
- * J is caller-provided scratch of 3 planes; it holds the step's -alpha*flux sums on exit. */
+ * J is caller-provided scratch of 3 planes; on exit it holds what was added to e:
+ * the step's -alpha*flux sums, smoothed when smoothing is on. */
 void orc_step(const orc_grid *g, double *e, double *b, double *J, int nsp, const orc_species *sp) {
     long nc = ncell(g);
     memset(J, 0, sizeof(double) * 3 * nc);
@@ -484,6 +525,7 @@ void orc_step(const orc_grid *g, double *e, double *b, double *J, int nsp, const
     }
     orc_b_advance(g, e, b, 0.5 * g->dt);                          /* 4, 5 */
     orc_e_advance(g, e, b, g->dt);                                /* 6, 7 */
+    if (g->smooth_passes > 0) orc_smooth(g, J, 3, g->smooth_passes);   /* 10 */
     for (long c = 0; c < 3 * nc; ++c) e[c] += J[c];               /* 11, 12 */
     wall_e(g, e);
 }

@@ -428,3 +428,101 @@ def test_thermal_plasma_k0_oscillation_is_at_the_relativistic_cutoff():
     factor = integrate.quad(f, 0, np.inf, limit=400)[0] / integrate.quad(w, 0, np.inf, limit=400)[0]
     omega_cut = np.sqrt(2.0) / n_x * np.sqrt(factor)
     assert abs(peak / omega_cut - 1) <= 0.03, (peak, omega_cut)
+
+
+# ---------------------------------------------------------------- current smoothing (App. A.3.4)
+
+def _printed_smoothing_weights():
+    """Weight by number of shifted indices, as printed in App. A.3.4 (golden fixture)."""
+    import os
+    w = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "current_smoothing_weights.txt")
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if f:
+            w[int(f[0])] = float(f[1])
+    return w
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_smoothing_impulse_response_is_the_printed_weights(ndim):
+    """A unit value spread by one pass: every neighbour receives its printed
+    weight divided by the sum of the 27 weights.  In 2D3V the z neighbours are
+    the cell itself (z ignorable), so their weights land on the same plane."""
+    w = _printed_smoothing_weights()
+    st = _state(ndim, (7, 6, 5))
+    nz, ny, nx = st.e.shape[1:]
+    c = (2, 3, 4) if ndim == 3 else (0, 3, 4)            # (k, j, i), the second near the edge
+    a = np.zeros((nz, ny, nx))
+    a[c] = 1.0
+    expect = np.zeros_like(a)
+    total = sum(w[(di != 0) + (dj != 0) + (dk != 0)]
+                for dk in (-1, 0, 1) for dj in (-1, 0, 1) for di in (-1, 0, 1))
+    for dk in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            for di in (-1, 0, 1):
+                q = ((c[0] + dk) % nz, (c[1] + dj) % ny, (c[2] + di) % nx)
+                expect[q] += w[(di != 0) + (dj != 0) + (dk != 0)] / total
+    out = oracle.smooth(st, a)
+    assert np.abs(out - expect).max() <= 1e-16
+    assert abs(out.sum() - 1.0) <= 1e-15
+
+
+@pytest.mark.parametrize("ndim,passes", [(2, 1), (3, 1), (3, 2)])
+def test_smoothing_transfer_function_is_a_product_of_cos_squared(ndim, passes):
+    """A Fourier mode of wavenumbers (m_x, m_y, m_z) is an eigenvector of one
+    pass with eigenvalue prod_a cos^2(pi m_a / n_a) (the 1-2-1 stencil per
+    axis); the Nyquist mode m_x = n_x/2 is removed."""
+    st = _state(ndim, (12, 10, 8))
+    nz, ny, nx = st.e.shape[1:]
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for m in [(0, 0, 0), (1, 0, 0), (2, 3, 1), (5, 4, 3), (6, 5, 4)]:
+        mz = m[2] if ndim == 3 else 0
+        a = np.cos(2 * np.pi * (m[0] * i / nx + m[1] * j / ny + mz * k / nz) + 0.3)
+        H = np.cos(np.pi * m[0] / nx) ** 2 * np.cos(np.pi * m[1] / ny) ** 2 * np.cos(np.pi * mz / nz) ** 2
+        out = oracle.smooth(st, a, passes)
+        assert np.abs(out - H ** passes * a).max() <= 1e-14, m
+
+
+@pytest.mark.parametrize("ndim,passes", [(2, 1), (3, 1), (2, 2)])
+def test_smoothed_step_conserves_the_smoothed_gauss_law(ndim, passes):
+    """With the current smoothed by S before it is added to e (main-loop step
+    10), a step conserves div e - S rho~ to round-off: S is a translation-
+    invariant stencil, so it commutes with the discrete divergence.  The
+    unsmoothed residual div e - rho~ then changes at the level of the charge."""
+    shape = (10, 9, 8)
+    arr = synth.random_state_arrays(31 + ndim + passes, ndim, *shape, ppc=6, spread=2.0,
+                                    amp_e=0.01, amp_b=0.01, colocate=False)
+    st = oracle.State.empty(ndim, *shape, dt=0.5, n_x=2.0, rho_sp0=8.0, smooth_passes=passes)
+    st.e[:] = arr["e"]
+    st.b[:] = arr["b"]
+    for s in arr["species"]:
+        st.species.append(oracle.Species(s["pos"], s["u"], s["q_over_e"], s["m_over_me"]))
+    rmax = max(np.abs(oracle.rho(st, s)).max() for s in range(2))
+    smoothed0 = oracle.div_e(st) - oracle.smooth(st, oracle.rho(st), passes)
+    raw0 = oracle.div_e(st) - oracle.rho(st)
+    for _ in range(4):
+        oracle.step(st)
+        smoothed1 = oracle.div_e(st) - oracle.smooth(st, oracle.rho(st), passes)
+        assert np.abs(smoothed1 - smoothed0).max() <= 1e-12 * rmax
+    raw1 = oracle.div_e(st) - oracle.rho(st)
+    assert np.abs(raw1 - raw0).max() > 1e-3 * rmax
+    assert oracle.gauss_residual(st)[0] == pytest.approx(np.abs(smoothed1).max(), rel=0, abs=0)
+
+
+def test_smoothing_off_leaves_the_step_unchanged():
+    """smooth_passes = 0 is the unsmoothed scheme, bit for bit."""
+    shape = (8, 6, 1)
+    arr = synth.random_state_arrays(41, 2, *shape, ppc=4, spread=1.0, amp_e=0.01, amp_b=0.01, colocate=False)
+    out = []
+    for passes in (0, 1):
+        st = oracle.State.empty(2, *shape, dt=0.5, n_x=2.0, rho_sp0=8.0, smooth_passes=passes)
+        st.e[:] = arr["e"]
+        st.b[:] = arr["b"]
+        for s in arr["species"]:
+            st.species.append(oracle.Species(s["pos"].copy(), s["u"].copy(), s["q_over_e"], s["m_over_me"]))
+        J = oracle.step(st)
+        out.append((st.e.copy(), J))
+    st0 = oracle.State.empty(2, *shape, dt=0.5, n_x=2.0, rho_sp0=8.0)
+    assert np.array_equal(out[1][1], oracle.smooth(st0, out[0][1], 1))
+    assert not np.array_equal(out[0][0], out[1][0])
