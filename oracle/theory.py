@@ -29,3 +29,26 @@ def tau_filamentation_pair(beta0):
 def tau_filamentation_electron_beams(beta0):
     G0 = 1.0 / np.sqrt(1.0 - beta0 * beta0)
     return np.sqrt(G0) / beta0 / (2.0 * np.pi)
+
+
+def cold_plasma_frequency(mass_ratio):
+    """omega_P / omega_pe of an electron-ion plasma with m_i / m_e = mass_ratio."""
+    return np.sqrt(1.0 + 1.0 / mass_ratio)
+
+
+def cold_cutoffs_heavy_ions(wce):
+    """(omega_L, omega_R) / omega_pe for infinitely heavy ions; wce = omega_ce / omega_pe."""
+    s = np.sqrt(wce * wce + 4.0)
+    return 0.5 * (s - wce), 0.5 * (s + wce)
+
+
+def cold_cutoffs_two_species(wce, mass_ratio):
+    """(omega_L, omega_R) / omega_pe with ions of mass mass_ratio * m_e: the
+    positive roots of R(omega) = 0, multiplied out to the cubic
+    omega (omega - wce)(omega + wci) - (omega + wci) - (omega - wce) / mass_ratio = 0,
+    wci = wce / mass_ratio.  Its roots are omega_R, 0 and -omega_L (L(omega) = R(-omega))."""
+    wci = wce / mass_ratio
+    cubic = (np.poly1d([1.0, -wce, 0.0]) * np.poly1d([1.0, wci]) - np.poly1d([1.0, wci])
+             - np.poly1d([1.0, -wce]) / mass_ratio)
+    roots = np.sort(cubic.roots.real)
+    return -roots[0], roots[-1]

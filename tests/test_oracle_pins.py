@@ -526,3 +526,53 @@ def test_smoothing_off_leaves_the_step_unchanged():
     st0 = oracle.State.empty(2, *shape, dt=0.5, n_x=2.0, rho_sp0=8.0)
     assert np.array_equal(out[1][1], oracle.smooth(st0, out[0][1], 1))
     assert not np.array_equal(out[0][0], out[1][0])
+
+
+# ---------------------------------------------------------------- magnetized cold modes (Sect. 3.1.2)
+
+def _spectral_peak(omega, spec, mask):
+    """Frequency of the largest value of spec inside mask, refined by a parabola
+    through the logarithms of the three bins around it."""
+    idx = np.where(mask)[0]
+    i = idx[np.argmax(spec[idx])]
+    a, b, c = np.log(spec[i - 1]), np.log(spec[i]), np.log(spec[(i + 1) % len(spec)])
+    return omega[i] + 0.5 * (a - c) / (a - 2 * b + c) * (omega[1] - omega[0])
+
+
+def test_magnetized_plasma_k0_modes_are_the_cold_cutoffs():
+    """Sect. 3.1.2: in a thermal electron-ion plasma (m_i/m_e = 49, v_th = 0.04 c)
+    with a uniform b0 along z, the electrons' total momentum oscillates at
+    omega_P along b0 and at the cut-offs omega_L, omega_R across it.  The
+    transverse spectrum is taken of sum (u_x + i u_y): electrons gyrate in the
+    positive sense about +z, so the R cut-off (same sense) appears at +omega_R and
+    the L cut-off (opposite sense) at -omega_L, which pins the sense of the
+    magnetic rotation.  omega_ce = 2 omega_pe, 8^2 cells, 16 cells per c/omega_pe,
+    60 plasma periods (bins of 0.017 omega_pe); the ions' finite mass moves
+    omega_L by 0.04 omega_pe from the heavy-ion formula, 3 bins."""
+    from oracle import mj, theory
+    wce, mu, theta_e, ppc, nx, n_x, dt = 2.0, 49.0, 0.0016, 8, 8, 16.0, 0.5
+    nsteps = int(round(60 * 2 * np.pi * n_x / dt))
+    n = ppc * nx * nx
+    st = oracle.State.empty(2, nx, nx, 1, dt, n_x, 2.0 * ppc)
+    pos, ue = mj.load(21, 0, n, theta_e, (0.0, 0.0, 0.0), 2, nx, nx, 1)
+    _, ui = mj.load(22, 1, n, theta_e / mu, (0.0, 0.0, 0.0), 2, nx, nx, 1)
+    st.species.append(oracle.Species(pos, ue, -1.0, 1.0))
+    st.species.append(oracle.Species(pos.copy(), ui, 1.0, mu))
+    st.b[2][:] = wce / n_x                  # b = omega_ce X0 / c
+    oracle.stagger_back(st)
+    Z = np.zeros(nsteps, complex)
+    Uz = np.zeros(nsteps)
+    for k in range(nsteps):
+        oracle.step(st)
+        u = st.species[0].u
+        Z[k] = u[0].sum() + 1j * u[1].sum()
+        Uz[k] = u[2].sum()
+    win = np.hanning(nsteps)
+    omega = 2 * np.pi * np.fft.fftfreq(nsteps, dt) * n_x      # units of omega_pe
+    S = np.abs(np.fft.fft((Z - Z.mean()) * win)) ** 2
+    Sz = np.abs(np.fft.fft((Uz - Uz.mean()) * win)) ** 2
+    wl, wr = theory.cold_cutoffs_two_species(wce, mu)
+    wp = theory.cold_plasma_frequency(mu)
+    assert abs(_spectral_peak(omega, S, omega > 0.2) - wr) <= 0.015
+    assert abs(_spectral_peak(omega, S, omega < -0.2) + wl) <= 0.015
+    assert abs(_spectral_peak(omega, Sz, omega > 0.2) - wp) <= 0.015

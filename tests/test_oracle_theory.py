@@ -30,3 +30,29 @@ def test_electron_beam_variant_is_sqrt2_slower():
     b = np.sqrt(1 - 1 / 9.0)   # Gamma0 = 3
     assert np.isclose(theory.tau_filamentation_electron_beams(b), np.sqrt(2) * theory.tau_filamentation_pair(b))
     assert abs(theory.tau_filamentation_electron_beams(b) - 0.2924) < 5e-4
+
+
+def test_cold_mode_formulas_reproduce_table_cold_modes():
+    """The paper's theory columns are the heavy-ion formulas; its measured
+    peaks are the cut-offs with the ions' finite mass (m_i/m_e = 49), to the
+    table's two printed digits (spectral resolution 0.01 omega_pe)."""
+    for wce, w_par, w_l, w_r, th_p, th_l, th_r in _table("cold_modes_table.txt"):
+        assert abs(theory.cold_plasma_frequency(49.0) - th_p) <= 5e-4
+        hl, hr = theory.cold_cutoffs_heavy_ions(wce)
+        assert abs(hl - th_l) <= 5e-3 and abs(hr - th_r) <= 5e-3, (wce, hl, hr)
+        ml, mr = theory.cold_cutoffs_two_species(wce, 49.0)
+        assert abs(ml - w_l) <= 0.011 and abs(mr - w_r) <= 0.021, (wce, ml, mr)
+        assert abs(theory.cold_plasma_frequency(49.0) - w_par) <= 0.005
+
+
+def test_two_species_cutoffs_tend_to_the_heavy_ion_formulas():
+    for wce in (0.3, 1.0, 3.0):
+        a = theory.cold_cutoffs_two_species(wce, 1e9)
+        b = theory.cold_cutoffs_heavy_ions(wce)
+        assert np.allclose(a, b, rtol=1e-7)
+        # R(omega_R) = 0 and L(omega_L) = 0 with the ions' terms
+        mu = 49.0
+        wl, wr = theory.cold_cutoffs_two_species(wce, mu)
+        R = 1 - 1 / (wr * (wr - wce)) - (1 / mu) / (wr * (wr + wce / mu))
+        L = 1 - 1 / (wl * (wl + wce)) - (1 / mu) / (wl * (wl - wce / mu))
+        assert abs(R) < 1e-10 and abs(L) < 1e-10
