@@ -81,7 +81,8 @@ def _oracle_state(w, seed, nx, ny, nz):
     from oracle import mj
     ncell = nx * ny * (nz if w["ndim"] == 3 else 1)
     n = int(round(w["ppc"] * ncell))
-    st = oracle.State.empty(w["ndim"], nx, ny, nz, w["dt"], w["n_x"], w["rho_sp0"])
+    st = oracle.State.empty(w["ndim"], nx, ny, nz, w["dt"], w["n_x"], w["rho_sp0"],
+                            smooth_passes=w.get("smooth", 0))
     pos, u0 = mj.load(seed, 0, n, w["theta"], (0.0, 0.0, 0.0), w["ndim"], nx, ny, nz)
     _, u1 = mj.load(seed + 1, 1, n, w["theta"], (0.0, 0.0, 0.0), w["ndim"], nx, ny, nz)
     st.species.append(oracle.Species(np.ascontiguousarray(pos), np.ascontiguousarray(u0), -1.0, 1.0))
@@ -148,7 +149,7 @@ def _time_oracle_sample(w, steps, seed):
     sw = dict(w)
     if w.get("ensemble"):   # one representative member of the ensemble
         w = sw = dict(ndim=2, nx=64, ny=64, nz=1, ppc=32, theta=0.1, n_x=0.1 ** -0.5, rho_sp0=64.0, dt=0.5,
-                      name=w["name"])
+                      name=w["name"], smooth=w.get("smooth", 0))
     elif w["ndim"] == 3:
         sw.update(nx=32, ny=32, nz=32)
     else:
@@ -237,13 +238,13 @@ def run_ours(args, w):
             n = m["ppc"] * m["nx"] * m["ny"]
             npart += 2 * n
             descs.append(pic.run_desc(2, m["nx"], m["ny"], 1, m["n_x"], m["rho_sp0"], w["dt"],
-                                      [(-1.0, 1.0, n), (1.0, 1.0, n)]))
+                                      [(-1.0, 1.0, n), (1.0, 1.0, n)], smooth_passes=args.smooth))
     else:
         members = None
         nz = 1 if w["ndim"] == 2 else w["nz"]
         n = int(round(w["ppc"] * w["nx"] * w["ny"] * nz))
         descs = [pic.run_desc(w["ndim"], w["nx"], w["ny"], nz, w["n_x"], w["rho_sp0"], w["dt"],
-                              [(-1.0, 1.0, n), (1.0, 1.0, n)])]
+                              [(-1.0, 1.0, n), (1.0, 1.0, n)], smooth_passes=args.smooth)]
         npart = 2 * n
 
     def load_all(ctx):
@@ -310,11 +311,13 @@ def run_ours(args, w):
             ms_t = ms
         push_ms, push_n = ctx.kernel_time(pic.PIC_KERNEL_PUSH)
         field_ms, field_n = ctx.kernel_time(pic.PIC_KERNEL_FIELD)
+        smooth_ms, smooth_n = ctx.kernel_time(pic.PIC_KERNEL_SMOOTH)
         sort_ms, sort_n = ctx.kernel_time(pic.PIC_KERNEL_SORT, reset=True)
         diag = ctx.diagnostics(0)
         ms = max_over_ranks(ms, dist, "cuda")
+        ncell = sum(d.nx * d.ny * d.nz for d in descs)
         results[name] = dict(ms=ms, ms_direct=ms_t, steps=steps, push_ms=push_ms, push_n=push_n, field_ms=field_ms,
-                             sort_ms=sort_ms, counters=cnt, clocks=clk, diag=diag,
+                             smooth_ms=smooth_ms, ncell=ncell, sort_ms=sort_ms, counters=cnt, clocks=clk, diag=diag,
                              tuning=dict(ctx.tuning(), autotune=tuned) if prec == pic.PIC_MIXED else None)
         ctx.close()
         del ctx
@@ -405,6 +408,16 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
             "clocks": m["clocks"],
             "diag": {"gauss_max": m["diag"]["gauss_max"], "rho_max": m["diag"]["rho_max"]},
         }
+        if args.smooth > 0:
+            # current smoothing: fold + passes, each 3 x 8 B read + 3 x 8 B written per cell
+            bytes_step = 48.0 * m["ncell"] * (1 + args.smooth)
+            sm_ms = m["smooth_ms"] / m["steps"]
+            ach = bytes_step / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
+            out["config"]["smooth_passes"] = args.smooth
+            out["roofline"]["smooth"] = {
+                "kernels": "k_fold + %d x k_smooth" % args.smooth, "passes": args.smooth, "ms_per_step": sm_ms,
+                "algorithmic_bytes_per_step": bytes_step, "achieved": ach, "unit": "GB/s",
+                "frac": None if ach is None else ach / peak}
         if not args.no_cpu_baseline:
             v, dt, npp, nst, sw = _time_oracle_sample(w, 1, seed=77)
             out["cpu_baseline"] = {"value": v, "unit": "particle-steps/ns", "cores": 1, "kind": "oracle",
@@ -430,10 +443,16 @@ def main():
     ap.add_argument("--tile", type=int, nargs=3, default=(0, 0, 0))
     ap.add_argument("--sort-interval", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--smooth", type=int, default=0, help="current smoothing passes per step (0..4, default off)")
     ap.add_argument("--autotune-steps", type=int, default=120)
     args = ap.parse_args()
     args.tile = tuple(args.tile)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if not 0 <= args.smooth <= 4:
+        ap.error("--smooth takes 0..4 passes")
+    w["smooth"] = args.smooth
+    if args.smooth:
+        w["name"] += ", current smoothing %d pass%s" % (args.smooth, "es" if args.smooth > 1 else "")
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

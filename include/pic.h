@@ -34,7 +34,7 @@ extern "C" {
 #endif
 
 #define PIC_MAX_SPECIES 4
-#define PIC_ABI_VERSION 1
+#define PIC_ABI_VERSION 2
 
 typedef enum {
     PIC_OK = 0,
@@ -57,7 +57,7 @@ typedef enum { PIC_MJ_EXACT = 0, PIC_MJ_MLP = 1, PIC_MJ_NAIVE_BOOST = 2 } pic_mj
 #define PIC_FLAG_TIMING 4u     /* record CUDA events around each kernel class (see pic_kernel_time) */
 
 /* Kernel classes timed under PIC_FLAG_TIMING. */
-typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_FIELD = 1, PIC_KERNEL_SORT = 2 } pic_kernel_class;
+typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_FIELD = 1, PIC_KERNEL_SORT = 2, PIC_KERNEL_SMOOTH = 3 } pic_kernel_class;
 
 /* Device memory provider.  alloc returns a device pointer of at least `bytes`
  * bytes aligned to 256 bytes, or NULL; free receives the same pointer and size. */
@@ -83,7 +83,13 @@ typedef struct {
  *  rho_sp0   reference superparticles per cell, all species together; with
  *            n_x it fixes the current coupling alpha_s = 2 sgn(q_s)/(n_x^2 rho_sp0) (Eq. alpha)
  *  dt        time step in X0/c; must satisfy dt < 1/sqrt(ndim) (Courant, App. B.1)
- *  bc        per axis: PIC_BC_PERIODIC, or PIC_BC_CONDUCTOR for x only (App. A.4) */
+ *  bc        per axis: PIC_BC_PERIODIC, or PIC_BC_CONDUCTOR for x only (App. A.4)
+ *  smooth_passes
+ *            current smoothing (App. A.3.4, main-loop step 10) applied this many
+ *            times per step, 0..4 (0: off).  One pass replaces the periodic current
+ *            of each cell by the mean of its 3x3x3 neighbourhood weighted 1, 1/2,
+ *            1/4, 1/8 by the number of shifted indices (the 1-2-1 stencil per
+ *            axis).  Periodic axes only: PIC_EINVAL with a conductor. */
 typedef struct {
     int ndim;
     int nx, ny, nz;
@@ -93,6 +99,7 @@ typedef struct {
     int bc[3];
     int nspecies;
     pic_species_desc species[PIC_MAX_SPECIES];
+    int smooth_passes;
 } pic_run_desc;
 
 /* Options of a context.
@@ -145,7 +152,9 @@ typedef struct {
  *  sum_u[s][c]     sum over particles of u_c (= sum gamma v_c, the k = 0
  *                  momentum of Eq. Fourier)
  *  temperature[s]  <u . v> / 3 (equals Theta for a Maxwell-Juttner plasma)
- *  gauss_max       max over nodes of |div e - rho~|, rho~ = sum_s alpha_s W (CIC)
+ *  gauss_max       max over nodes of |div e - S rho~|, rho~ = sum_s alpha_s W (CIC),
+ *                  S the run's current smoothing (identity when off): smoothing the
+ *                  current conserves div e - S rho~
  *  rho_max         max over species and nodes of |rho~_s|
  *  nonfinite       number of non-finite values met in fields and particles */
 typedef struct {

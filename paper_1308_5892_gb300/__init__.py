@@ -21,7 +21,7 @@ PIC_BC_PERIODIC, PIC_BC_CONDUCTOR = 0, 1
 PIC_PROFILE_UNIFORM, PIC_PROFILE_HARRIS = 0, 1
 PIC_MJ_EXACT, PIC_MJ_MLP, PIC_MJ_NAIVE_BOOST = 0, 1, 2
 PIC_FLAG_ASYNC, PIC_FLAG_NO_GRAPH, PIC_FLAG_TIMING = 1, 2, 4
-PIC_KERNEL_PUSH, PIC_KERNEL_FIELD, PIC_KERNEL_SORT = 0, 1, 2
+PIC_KERNEL_PUSH, PIC_KERNEL_FIELD, PIC_KERNEL_SORT, PIC_KERNEL_SMOOTH = 0, 1, 2, 3
 MAX_SPECIES = 4
 
 ABI_FUNCTIONS = [
@@ -47,7 +47,8 @@ class SpeciesDesc(ctypes.Structure):
 class RunDesc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("n_x", ctypes.c_double), ("rho_sp0", ctypes.c_double), ("dt", ctypes.c_double),
-                ("bc", ctypes.c_int * 3), ("nspecies", ctypes.c_int), ("species", SpeciesDesc * MAX_SPECIES)]
+                ("bc", ctypes.c_int * 3), ("nspecies", ctypes.c_int), ("species", SpeciesDesc * MAX_SPECIES),
+                ("smooth_passes", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -139,9 +140,11 @@ def lib(build_if_missing=True):
     return L
 
 
-def run_desc(ndim, nx, ny, nz, n_x, rho_sp0, dt, species, bc=(0, 0, 0)):
-    """species: list of (q_over_e, m_over_me, capacity)."""
+def run_desc(ndim, nx, ny, nz, n_x, rho_sp0, dt, species, bc=(0, 0, 0), smooth_passes=0):
+    """species: list of (q_over_e, m_over_me, capacity); smooth_passes: current
+    smoothing passes per step (App. A.3.4), 0 = off."""
     d = RunDesc()
+    d.smooth_passes = smooth_passes
     d.ndim, d.nx, d.ny, d.nz = ndim, nx, ny, nz
     d.n_x, d.rho_sp0, d.dt = n_x, rho_sp0, dt
     for a in range(3):

@@ -61,6 +61,8 @@ struct Run {
     int *offsets = nullptr, *block_sums = nullptr;
     int *perm = nullptr;        // sort scratch, max species capacity
     double *rho_s = nullptr, *rho_tot = nullptr, *divb = nullptr;
+    int smooth = 0;             // current smoothing passes per step (App. A.3.4)
+    double *sbuf[2] = {nullptr, nullptr};   // compact FP64 smoothing buffers, 3 planes each
     double *acc = nullptr;      // diagnostics accumulators (64 doubles)
     double *hist = nullptr;     // energy history, 8 doubles per step
     int64_t hist_cap = 0, hist_n = 0;
@@ -70,6 +72,8 @@ struct Run {
 };
 
 }  // namespace
+
+constexpr int kKernelClasses = 4;   // PIC_KERNEL_PUSH .. PIC_KERNEL_SMOOTH
 
 struct pic_ctx {
     int precision = PIC_FP64;
@@ -121,10 +125,10 @@ struct pic_ctx {
     cudaEvent_t io_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // start, loaded/filled[2], consumed/copied[2]
     std::vector<FieldRunF> h_fe, h_fp;
     // PIC_FLAG_TIMING: event pairs per kernel class, resolved in pic_kernel_time
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[3];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[kKernelClasses];
     std::vector<cudaEvent_t> ev_pool;
-    double ev_ms[3] = {0, 0, 0};
-    int64_t ev_n[3] = {0, 0, 0};
+    double ev_ms[kKernelClasses] = {0, 0, 0, 0};
+    int64_t ev_n[kKernelClasses] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -276,8 +280,8 @@ __global__ void k_upload_mixed(Geom g, const double *st, long long m, long long 
             c[ax] = ci;
             o[ax] = off;
         }
-        for (int a = 3; a < 6; ++a)
-            if (!isfinite(st[a * m + q])) atomicOr(err, ERR_NONFINITE);
+        for (int comp = 3; comp < 6; ++comp)
+            if (!isfinite(st[comp * m + q])) atomicOr(err, ERR_NONFINITE);
         d.cell[a + q] = pack_cell(g.ndim, c[0], c[1], c[2]);
         d.off[0][a + q] = o[0];
         d.off[1][a + q] = o[1];
@@ -373,6 +377,11 @@ bool validate(const pic_run_desc &d, int precision, std::string &why) {
     for (int a = 0; a < 3; ++a) {
         if (d.bc[a] != PIC_BC_PERIODIC && d.bc[a] != PIC_BC_CONDUCTOR) { why = "unknown boundary kind"; return false; }
         if (a > 0 && d.bc[a] != PIC_BC_PERIODIC) { why = "conducting walls are supported along x only"; return false; }
+    }
+    if (d.smooth_passes < 0 || d.smooth_passes > 4) { why = "smooth_passes must be 0..4"; return false; }
+    if (d.smooth_passes > 0 && d.bc[0] != PIC_BC_PERIODIC) {
+        why = "current smoothing is defined for periodic axes only";
+        return false;
     }
     return true;
 }
@@ -532,6 +541,13 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     r.hist_idx = (long long *)dev_alloc(ctx, sizeof(long long));
     if (!r.rho_s || !r.rho_tot || !r.divb || !r.acc || !r.hist || !r.hist_idx)
         return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the diagnostics buffers");
+    r.smooth = d.smooth_passes;
+    if (r.smooth > 0) {
+        for (int b = 0; b < 2; ++b) {
+            r.sbuf[b] = (double *)dev_alloc(ctx, sizeof(double) * 3 * ncell);
+            if (!r.sbuf[b]) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the smoothing buffers");
+        }
+    }
     CK(cudaMemsetAsync(r.hist, 0, sizeof(double) * 8 * r.hist_cap, ctx->stream));
     CK(cudaMemsetAsync(r.hist_idx, 0, sizeof(long long), ctx->stream));
     for (int s = 0; s < d.nspecies; ++s) {
@@ -697,6 +713,9 @@ FieldRunF field_run(Run &r, bool energy, bool inc) {
     fr.hist = energy ? hist_ref(r) : HistRef{nullptr, nullptr, 0};
     fr.hist_inc = inc ? r.hist_idx : nullptr;
     fr.scale = 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0) * 0x1p-36;
+    fr.smooth = r.smooth;
+    fr.sbuf[0] = r.sbuf[0];
+    fr.sbuf[1] = r.sbuf[1];
     return fr;
 }
 
@@ -796,6 +815,15 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
             for (auto &r : ctx->runs)
                 for (int q = 0; q < r.d.nspecies; ++q) r.sp[q].counted = true;
     }
+    int max_smooth = 0;
+    for (auto &r : ctx->runs) max_smooth = std::max(max_smooth, r.smooth);
+    if (max_smooth > 0) {
+        KTimer t(ctx, PIC_KERNEL_SMOOTH);
+        launch_smooth_multi(0, 0, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, s);
+        for (int p = 0; p < max_smooth; ++p)
+            launch_smooth_multi(1, p, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, s);
+        launches += 1 + max_smooth;
+    }
     {
         KTimer t(ctx, PIC_KERNEL_FIELD);
         launch_fields_multi(FIELD_B_HALF, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, 0.5f * dt, dt, s);
@@ -810,6 +838,16 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
     ctx->launch_total += launches + 5;
     ctx->bytes_per_ps = ctx->runs[0].d.ndim == 2 ? 48.0 : 56.0;
     return PIC_OK;
+}
+
+// Current smoothing of one run (main-loop step 10): folds the deposited current
+// J into sbuf[0] and applies the passes; returns the smoothed compact current,
+// or nullptr when the run does not smooth.
+template <typename JT>
+const double *smooth_current(pic_ctx *ctx, Run &r, JT *const J[3]) {
+    if (r.smooth <= 0) return nullptr;
+    KTimer t(ctx, PIC_KERNEL_SMOOTH);
+    return launch_smooth_current<JT>(r.g, J, r.smooth, r.sbuf, ctx->stream);
 }
 
 void step_run(pic_ctx *ctx, Run &r) {
@@ -833,13 +871,15 @@ void step_run(pic_ctx *ctx, Run &r) {
         double *Z[3] = {jplane<double>(r, 1 - r.jcur, 0), jplane<double>(r, 1 - r.jcur, 1),
                         jplane<double>(r, 1 - r.jcur, 2)};
         const double *Jc[3] = {J[0], J[1], J[2]};
+        const double *Js = smooth_current<double>(ctx, r, J);
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
             launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, HistRef{nullptr, nullptr, 0}, s);
-            launch_e_advance<double>(r.g, f, Jc, Z, r.d.dt, s);
+            if (Js) launch_e_advance_smoothed<double, double>(r.g, f, Js, 1.0, Z, r.d.dt, nullptr, s);
+            else launch_e_advance<double>(r.g, f, Jc, Z, r.d.dt, s);
         }
         ctx->bytes_per_ps = r.d.ndim == 2 ? 80.0 : 96.0;
-        ctx->launch_total += 3 + nsp;
+        ctx->launch_total += 3 + nsp + (Js ? r.smooth : 0);
     } else {
         int launches = 0;
         if (!r.sorted || r.since_sort >= r.sort_interval) {
@@ -893,14 +933,16 @@ void step_run(pic_ctx *ctx, Run &r) {
         }
         u64 *Z[3] = {jplane<u64>(r, 1 - r.jcur, 0), jplane<u64>(r, 1 - r.jcur, 1), jplane<u64>(r, 1 - r.jcur, 2)};
         const u64 *Jc[3] = {J[0], J[1], J[2]};
+        const double *Js = smooth_current<u64>(ctx, r, J);
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
+            const double alpha_abs = 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0);
             launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, HistRef{nullptr, nullptr, 0}, s);
-            launch_e_advance_fx(r.g, f, Jc, Z, (float)r.d.dt, 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0), r.hist_idx,
-                                s);
+            if (Js) launch_e_advance_smoothed<float, u64>(r.g, f, Js, alpha_abs * 0x1p-36, Z, (float)r.d.dt, r.hist_idx, s);
+            else launch_e_advance_fx(r.g, f, Jc, Z, (float)r.d.dt, alpha_abs, r.hist_idx, s);
         }
         r.since_sort++;
-        launches += 5;
+        launches += 5 + (Js ? 1 + r.smooth : 0);   // shell fold + passes
         ctx->launch_total += launches;
         ctx->bytes_per_ps = r.d.ndim == 2 ? 48.0 : 56.0;
     }
@@ -1152,7 +1194,7 @@ void pic_destroy(pic_ctx *ctx) {
     for (auto e : ctx->io_ev)
         if (e) cudaEventDestroy(e);
     if (ctx->gstage) cudaFreeHost(ctx->gstage);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < kKernelClasses; ++k)
         for (auto &pr : ctx->ev_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     for (auto &a : ctx->allocs) {
@@ -1428,7 +1470,15 @@ pic_status pic_diagnostics(pic_ctx *ctx, int run, pic_diag *out) {
     }
     if (ctx->precision == PIC_FP64) launch_div_e<double>(g, fields_of<double>(r), r.divb, sm);
     else launch_div_e<float>(g, fields_of<float>(r), r.divb, sm);
-    launch_max_abs_diff(r.divb, r.rho_tot, ncell, r.acc + 48, sm);
+    // with smoothing the conserved residual is div e - S rho~: smooth rho~ the
+    // same number of times, alternating with rho_s as scratch
+    double *rho_cmp = r.rho_tot;
+    for (int p = 0; p < r.smooth; ++p) {
+        double *other = rho_cmp == r.rho_tot ? r.rho_s : r.rho_tot;
+        launch_smooth(g, rho_cmp, other, sm);
+        rho_cmp = other;
+    }
+    launch_max_abs_diff(r.divb, rho_cmp, ncell, r.acc + 48, sm);
     CK(cudaGetLastError());
     double h[64];
     CK(cudaMemcpyAsync(h, r.acc, sizeof h, cudaMemcpyDeviceToHost, sm));
@@ -1611,9 +1661,9 @@ pic_status pic_get_counters(const pic_ctx *ctx, int64_t *launches_per_step, doub
 
 pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *total_ms, int64_t *launches) {
     if (!ctx) return PIC_EINVAL;
-    if (kernel_class < 0 || kernel_class > 2) return fail(ctx, PIC_EINVAL, "unknown kernel class");
+    if (kernel_class < 0 || kernel_class >= kKernelClasses) return fail(ctx, PIC_EINVAL, "unknown kernel class");
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKernelClasses; ++k) {
         for (auto &pr : ctx->ev_pending[k]) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) ctx->ev_ms[k] += ms;
@@ -1626,7 +1676,7 @@ pic_status pic_kernel_time(pic_ctx *ctx, int kernel_class, int reset, double *to
     if (total_ms) *total_ms = ctx->ev_ms[kernel_class];
     if (launches) *launches = ctx->ev_n[kernel_class];
     if (reset) {
-        for (int k = 0; k < 3; ++k) { ctx->ev_ms[k] = 0; ctx->ev_n[k] = 0; }
+        for (int k = 0; k < kKernelClasses; ++k) { ctx->ev_ms[k] = 0; ctx->ev_n[k] = 0; }
     }
     return PIC_OK;
 }

@@ -129,6 +129,21 @@ void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long 
                          cudaStream_t s);
 template <typename R>
 void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s);
+// e += dt curl b + scale * Js with the smoothed compact current Js (3 planes of
+// nx*ny*nz doubles, in the units of the path's current), and zeroing of Jzero
+template <typename R, typename ZT>
+void launch_e_advance_smoothed(const Geom &g, FieldPtrs<R> f, const double *Js, double scale, ZT *const Jzero[3],
+                               R dt, long long *hist_inc, cudaStream_t s);
+
+// smooth.cu: current smoothing (App. A.3.4).  Compact arrays are indexed
+// (k*ny + j)*nx + i over the interior, plane after plane.
+// Smooths the deposited current J (padded planes; its ghost images are folded
+// into the interior in place, so J is consumed) `passes` >= 1 times into the
+// compact buffers buf[0..1] (3 planes each); returns the buffer with the result.
+template <typename JT>
+const double *launch_smooth_current(const Geom &g, JT *const J[3], int passes, double *const buf[2], cudaStream_t s);
+// one smoothing pass of one compact plane, in -> out (distinct arrays)
+void launch_smooth(const Geom &g, const double *in, double *out, cudaStream_t s);
 
 // push_fp64.cu
 void launch_push_fp64(const Geom &g, FieldPtrs<double> f, double *const J[3], Species64 sp, long long n,
@@ -178,10 +193,16 @@ struct FieldRunF {
     HistRef hist;           // slot[2..7]: e^2, b^2 sums of the step (null base: none)
     long long *hist_inc;    // E_FX phase: step counter of the history, incremented once (nullable)
     double scale;           // |alpha| 2^-36
+    int smooth;             // current smoothing passes (0: off); the E_FX phase then reads sbuf[smooth & 1]
+    double *sbuf[2];        // compact FP64 smoothing buffers, 3 planes of nx*ny*nz each
 };
 enum { FIELD_B_HALF = 0, FIELD_NODE = 1, FIELD_E_FX = 2 };
 void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_prefix_dev, int nblocks, int nruns,
                          float h, float dt, cudaStream_t s);
+// smooth.cu, batched: phase 0 folds every smoothing run's J into sbuf[0]; phase 1 runs pass
+// `pass` (sbuf[pass & 1] -> sbuf[(pass + 1) & 1]) of the runs with more passes
+void launch_smooth_multi(int phase, int pass, const FieldRunF *runs_dev, const int *block_prefix_dev, int nblocks,
+                         int nruns, cudaStream_t s);
 void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
                             float h, float dt, cudaStream_t s);
 size_t mixed_smem_bytes(const TileGeom &t, int ndim);

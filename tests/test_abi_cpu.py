@@ -25,7 +25,7 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L, n), n
     assert set(names) <= set(pic.ABI_FUNCTIONS) | {n for n in names if n.startswith("pic_")}
-    assert L.pic_abi_version() == 1
+    assert L.pic_abi_version() == 2
 
 
 def _init(desc, precision=pic.PIC_FP64):
@@ -48,12 +48,16 @@ def _init(desc, precision=pic.PIC_FP64):
     (dict(species=[(-1.0, 0.0, 10)]), "zero mass"),
     (dict(species=[(-1.0, 1.0, -5)]), "negative capacity"),
     (dict(bc=(0, 1, 0)), "conductor along y"),
+    (dict(smooth_passes=5), "too many smoothing passes"),
+    (dict(smooth_passes=-1), "negative smoothing passes"),
+    (dict(smooth_passes=1, bc=(1, 0, 0)), "smoothing with a conductor"),
 ])
 def test_init_rejects_invalid_descriptors(kw, why):
-    args = dict(ndim=2, nx=16, ny=16, nz=1, n_x=2.0, rho_sp0=8.0, dt=0.5, species=[(-1.0, 1.0, 10)], bc=(0, 0, 0))
+    args = dict(ndim=2, nx=16, ny=16, nz=1, n_x=2.0, rho_sp0=8.0, dt=0.5, species=[(-1.0, 1.0, 10)], bc=(0, 0, 0),
+                smooth_passes=0)
     args.update(kw)
     d = pic.run_desc(args["ndim"], args["nx"], args["ny"], args["nz"], args["n_x"], args["rho_sp0"], args["dt"],
-                     args["species"], args["bc"])
+                     args["species"], args["bc"], smooth_passes=args["smooth_passes"])
     st, h = _init(d)
     assert st == pic.PIC_EINVAL, why
     assert not h.value

@@ -289,3 +289,62 @@ def test_ensemble_field_fluctuation_level_scales_as_one_over_ppc():
     slope = np.polyfit(np.log(ppcs), np.log(level), 1)[0]
     print("fluctuation level by ppc:", dict(zip(ppcs, np.round(level, 6))), "slope %.3f" % slope)
     assert abs(slope + 1.0) <= 0.25, slope
+
+
+# ---------------------------------------------------------------- magnetized cold modes (Sect. 3.1.2)
+
+def _cold_table():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "cold_modes_table.txt")
+    return {row[0]: row for row in np.loadtxt(path, comments="#", ndmin=2)}
+
+
+def _peak(omega, spec, mask):
+    idx = np.where(mask)[0]
+    i = idx[np.argmax(spec[idx])]
+    a, b, c = np.log(spec[i - 1]), np.log(spec[i]), np.log(spec[(i + 1) % len(spec)])
+    return omega[i] + 0.5 * (a - c) / (a - 2 * b + c) * (omega[1] - omega[0])
+
+
+def _cold_modes(precision, wce, mu=49.0, theta_e=0.0016, ppc=16, nx=32, n_x=16.0, dt=0.5, periods=100, every=2):
+    """Peaks of the electrons' k = 0 momentum spectra: (+omega_R, -omega_L) of
+    sum (u_x + i u_y) and omega_P of sum u_z, in units of omega_pe."""
+    nsamp = int(round(periods * 2 * np.pi * n_x / dt)) // every
+    n = ppc * nx * nx
+    d = pic.run_desc(2, nx, nx, 1, n_x, 2.0 * ppc, dt, [(-1.0, 1.0, n), (1.0, mu, n)])
+    Z = np.zeros(nsamp, complex)
+    Uz = np.zeros(nsamp)
+    with pic.Context([d], precision=precision) as ctx:
+        ctx.set_uniform_field(0, (0.0, 0.0, 0.0), (0.0, 0.0, wce / n_x))   # b = omega_ce X0 / c along z
+        ctx.load_maxwell_juttner(0, 0, ppc, theta_e, (0.0, 0.0, 0.0), seed=31)
+        ctx.load_maxwell_juttner(0, 1, ppc, theta_e / mu, (0.0, 0.0, 0.0), colocate_with=0, seed=32)
+        for k in range(nsamp):
+            ctx.step(every)
+            su = ctx.diagnostics(0)["sum_u"][0]
+            Z[k] = su[0] + 1j * su[1]
+            Uz[k] = su[2]
+    win = np.hanning(nsamp)
+    omega = 2 * np.pi * np.fft.fftfreq(nsamp, every * dt) * n_x
+    S = np.abs(np.fft.fft((Z - Z.mean()) * win)) ** 2
+    Sz = np.abs(np.fft.fft((Uz - Uz.mean()) * win)) ** 2
+    return (_peak(omega, S, omega > 0.2), -_peak(omega, S, omega < -0.2), _peak(omega, Sz, omega > 0.2))
+
+
+@pytest.mark.parametrize("precision,wce", [(pic.PIC_MIXED, 1.0), (pic.PIC_MIXED, 2.0), (pic.PIC_FP64, 1.0)])
+def test_magnetized_cold_modes_match_theory_and_table(precision, wce):
+    """Table cold_modes (Sect. 3.1.2): a thermal electron-ion plasma (m_i/m_e =
+    49, v_th = 0.04 c) in a uniform b0 along z, 32^2 cells, 16 cells per
+    c/omega_pe (Debye length 0.64 cells), 16 ppc per species, 100 plasma periods
+    (bins of 0.01 omega_pe), as in the table.  The electrons' total momentum
+    peaks at omega_P along b0 and at the cut-offs across it, R at +omega_R and L
+    at -omega_L in the spectrum of sum (u_x + i u_y) (the sense of gyration).
+    Bars: 0.015 omega_pe against the cold two-species theory, and 0.025
+    against the peaks the paper measured."""
+    wr_m, wl_m, wp_m = _cold_modes(precision, wce)
+    wl, wr = theory.cold_cutoffs_two_species(wce, 49.0)
+    wp = theory.cold_plasma_frequency(49.0)
+    assert abs(wr_m - wr) <= 0.015, (wr_m, wr)
+    assert abs(wl_m - wl) <= 0.015, (wl_m, wl)
+    assert abs(wp_m - wp) <= 0.015, (wp_m, wp)
+    row = _cold_table()[wce]
+    assert abs(wp_m - row[1]) <= 0.025 and abs(wl_m - row[2]) <= 0.025 and abs(wr_m - row[3]) <= 0.025, row
