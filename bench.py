@@ -409,13 +409,15 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
             "diag": {"gauss_max": m["diag"]["gauss_max"], "rho_max": m["diag"]["rho_max"]},
         }
         if args.smooth > 0:
-            # current smoothing: fold + passes, each 3 x 8 B read + 3 x 8 B written per cell
-            bytes_step = 48.0 * m["ncell"] * (1 + args.smooth)
+            # current smoothing: each pass reads and writes 3 x 8 B per interior cell (the in-place
+            # fold of the ghost images touches only the boundary layers and is not counted)
+            bytes_step = 48.0 * m["ncell"] * args.smooth
             sm_ms = m["smooth_ms"] / m["steps"]
             ach = bytes_step / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
             out["config"]["smooth_passes"] = args.smooth
             out["roofline"]["smooth"] = {
-                "kernels": "k_fold + %d x k_smooth" % args.smooth, "passes": args.smooth, "ms_per_step": sm_ms,
+                "kernels": "k_fold_shell + %d x k_smooth_cols" % args.smooth if nruns == 1 else
+                           "k_smooth_multi (fold + %d passes)" % args.smooth, "passes": args.smooth, "ms_per_step": sm_ms,
                 "algorithmic_bytes_per_step": bytes_step, "achieved": ach, "unit": "GB/s",
                 "frac": None if ach is None else ach / peak}
         if not args.no_cpu_baseline:

@@ -62,7 +62,7 @@ struct Run {
     int *perm = nullptr;        // sort scratch, max species capacity
     double *rho_s = nullptr, *rho_tot = nullptr, *divb = nullptr;
     int smooth = 0;             // current smoothing passes per step (App. A.3.4)
-    double *sbuf[2] = {nullptr, nullptr};   // compact FP64 smoothing buffers, 3 planes each
+    void *sbuf[2] = {nullptr, nullptr};     // compact smoothing buffers, 3 planes of 8-byte values each
     double *acc = nullptr;      // diagnostics accumulators (64 doubles)
     double *hist = nullptr;     // energy history, 8 doubles per step
     int64_t hist_cap = 0, hist_n = 0;
@@ -544,7 +544,7 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     r.smooth = d.smooth_passes;
     if (r.smooth > 0) {
         for (int b = 0; b < 2; ++b) {
-            r.sbuf[b] = (double *)dev_alloc(ctx, sizeof(double) * 3 * ncell);
+            r.sbuf[b] = dev_alloc(ctx, 8 * 3 * ncell);
             if (!r.sbuf[b]) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the smoothing buffers");
         }
     }
@@ -714,8 +714,8 @@ FieldRunF field_run(Run &r, bool energy, bool inc) {
     fr.hist_inc = inc ? r.hist_idx : nullptr;
     fr.scale = 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0) * 0x1p-36;
     fr.smooth = r.smooth;
-    fr.sbuf[0] = r.sbuf[0];
-    fr.sbuf[1] = r.sbuf[1];
+    fr.sbuf[0] = (long long *)r.sbuf[0];
+    fr.sbuf[1] = (long long *)r.sbuf[1];
     return fr;
 }
 
@@ -844,10 +844,12 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
 // J into sbuf[0] and applies the passes; returns the smoothed compact current,
 // or nullptr when the run does not smooth.
 template <typename JT>
-const double *smooth_current(pic_ctx *ctx, Run &r, JT *const J[3]) {
+const typename SmoothValue<JT>::type *smooth_current(pic_ctx *ctx, Run &r, JT *const J[3]) {
+    typedef typename SmoothValue<JT>::type T;
     if (r.smooth <= 0) return nullptr;
     KTimer t(ctx, PIC_KERNEL_SMOOTH);
-    return launch_smooth_current<JT>(r.g, J, r.smooth, r.sbuf, ctx->stream);
+    T *const buf[2] = {(T *)r.sbuf[0], (T *)r.sbuf[1]};
+    return launch_smooth_current<JT>(r.g, J, r.smooth, buf, ctx->stream);
 }
 
 void step_run(pic_ctx *ctx, Run &r) {
@@ -875,7 +877,7 @@ void step_run(pic_ctx *ctx, Run &r) {
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
             launch_b_advance<double>(r.g, f, 0.5 * r.d.dt, HistRef{nullptr, nullptr, 0}, s);
-            if (Js) launch_e_advance_smoothed<double, double>(r.g, f, Js, 1.0, Z, r.d.dt, nullptr, s);
+            if (Js) launch_e_advance_smoothed<double, double, double>(r.g, f, Js, 1.0, Z, r.d.dt, nullptr, s);
             else launch_e_advance<double>(r.g, f, Jc, Z, r.d.dt, s);
         }
         ctx->bytes_per_ps = r.d.ndim == 2 ? 80.0 : 96.0;
@@ -933,12 +935,14 @@ void step_run(pic_ctx *ctx, Run &r) {
         }
         u64 *Z[3] = {jplane<u64>(r, 1 - r.jcur, 0), jplane<u64>(r, 1 - r.jcur, 1), jplane<u64>(r, 1 - r.jcur, 2)};
         const u64 *Jc[3] = {J[0], J[1], J[2]};
-        const double *Js = smooth_current<u64>(ctx, r, J);
+        const long long *Js = smooth_current<u64>(ctx, r, J);
         {
             KTimer t(ctx, PIC_KERNEL_FIELD);
             const double alpha_abs = 2.0 / (r.d.n_x * r.d.n_x * r.d.rho_sp0);
             launch_b_advance<float>(r.g, f, 0.5f * (float)r.d.dt, HistRef{nullptr, nullptr, 0}, s);
-            if (Js) launch_e_advance_smoothed<float, u64>(r.g, f, Js, alpha_abs * 0x1p-36, Z, (float)r.d.dt, r.hist_idx, s);
+            if (Js)
+                launch_e_advance_smoothed<float, u64, long long>(r.g, f, Js, alpha_abs * 0x1p-36, Z, (float)r.d.dt,
+                                                                 r.hist_idx, s);
             else launch_e_advance_fx(r.g, f, Jc, Z, (float)r.d.dt, alpha_abs, r.hist_idx, s);
         }
         r.since_sort++;

@@ -189,8 +189,8 @@ __global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long l
 // The same update with the smoothed current: Js holds 3 compact planes (nx*ny*nz
 // each, indexed (k*ny + j)*nx + i) in the units of the path's current, which
 // scale converts (1 in the FP64 path, |alpha| 2^-36 in the mixed path).
-template <typename R, typename ZT>
-__device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R> &f, const double *Js, double scale,
+template <typename R, typename ZT, typename CT>
+__device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R> &f, const CT *Js, double scale,
                                                 ZT *Z0, ZT *Z1, ZT *Z2, R dt, long long p) {
     int pi, pj, pk;
     padded_coords(g, p, pi, pj, pk);
@@ -202,9 +202,9 @@ __device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R
     const R curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
     const R curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
     const R curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
-    const R jx = (R)(scale * __ldg(Js + q));
-    const R jy = (R)(scale * __ldg(Js + ncell + q));
-    const R jz = (R)(scale * __ldg(Js + 2 * ncell + q));
+    const R jx = (R)(scale * (double)__ldg(Js + q));
+    const R jy = (R)(scale * (double)__ldg(Js + ncell + q));
+    const R jz = (R)(scale * (double)__ldg(Js + 2 * ncell + q));
     R ex = f.e[0][p] + dt * curl_x + jx;
     R ey = f.e[1][p] + dt * curl_y + jy;
     R ez = f.e[2][p] + dt * curl_z + jz;
@@ -217,13 +217,13 @@ __device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R
     Z2[p] = ZT(0);
 }
 
-template <typename R, typename ZT>
-__global__ void k_e_advance_smoothed(Geom g, FieldPtrs<R> f, const double *Js, double scale, ZT *Z0, ZT *Z1, ZT *Z2,
+template <typename R, typename ZT, typename CT>
+__global__ void k_e_advance_smoothed(Geom g, FieldPtrs<R> f, const CT *Js, double scale, ZT *Z0, ZT *Z1, ZT *Z2,
                                      R dt, long long *hist_inc) {
     if (hist_inc && blockIdx.x == 0 && threadIdx.x == 0) *hist_inc += 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride)
-        e_smoothed_cell<R, ZT>(g, f, Js, scale, Z0, Z1, Z2, dt, p);
+        e_smoothed_cell<R, ZT, CT>(g, f, Js, scale, Z0, Z1, Z2, dt, p);
 }
 
 // Staggered value read by the gather; with conductor walls a value located
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(256) k_fields_multi(const FieldRunF *runs, con
         if (r.hist_inc && blockIdx.x == block_prefix[run_sh] && threadIdx.x == 0) *r.hist_inc += 1;
         if (in) {
             if (r.smooth > 0)
-                e_smoothed_cell<float, unsigned long long>(r.g, r.f, r.sbuf[r.smooth & 1], r.scale, r.Z[0], r.Z[1],
-                                                           r.Z[2], dt, p);
+                e_smoothed_cell<float, unsigned long long, long long>(r.g, r.f, r.sbuf[r.smooth & 1], r.scale,
+                                                                      r.Z[0], r.Z[1], r.Z[2], dt, p);
             else
                 e_fx_cell(r.g, r.f, r.J[0], r.J[1], r.J[2], r.Z[0], r.Z[1], r.Z[2], dt, r.scale, p);
         }
@@ -364,11 +364,11 @@ void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long 
                                                            dt, alpha_abs * 0x1p-36, hist_inc);
 }
 
-template <typename R, typename ZT>
-void launch_e_advance_smoothed(const Geom &g, FieldPtrs<R> f, const double *Js, double scale, ZT *const Jzero[3],
+template <typename R, typename ZT, typename CT>
+void launch_e_advance_smoothed(const Geom &g, FieldPtrs<R> f, const CT *Js, double scale, ZT *const Jzero[3],
                                R dt, long long *hist_inc, cudaStream_t s) {
-    k_e_advance_smoothed<R, ZT><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, Js, scale, Jzero[0], Jzero[1],
-                                                                        Jzero[2], dt, hist_inc);
+    k_e_advance_smoothed<R, ZT, CT><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, Js, scale, Jzero[0], Jzero[1],
+                                                                            Jzero[2], dt, hist_inc);
 }
 
 template <typename R>
@@ -383,11 +383,13 @@ template void launch_e_advance<float>(const Geom &, FieldPtrs<float>, const floa
                                       cudaStream_t);
 template void launch_e_advance<double>(const Geom &, FieldPtrs<double>, const double *const[3], double *const[3],
                                        double, cudaStream_t);
-template void launch_e_advance_smoothed<double, double>(const Geom &, FieldPtrs<double>, const double *, double,
-                                                       double *const[3], double, long long *, cudaStream_t);
-template void launch_e_advance_smoothed<float, unsigned long long>(const Geom &, FieldPtrs<float>, const double *,
-                                                                   double, unsigned long long *const[3], float,
-                                                                   long long *, cudaStream_t);
+template void launch_e_advance_smoothed<double, double, double>(const Geom &, FieldPtrs<double>, const double *,
+                                                               double, double *const[3], double, long long *,
+                                                               cudaStream_t);
+template void launch_e_advance_smoothed<float, unsigned long long, long long>(const Geom &, FieldPtrs<float>,
+                                                                              const long long *, double,
+                                                                              unsigned long long *const[3], float,
+                                                                              long long *, cudaStream_t);
 template void launch_add_uniform<float>(const Geom &, FieldPtrs<float>, const double[3], const double[3],
                                         cudaStream_t);
 template void launch_add_uniform<double>(const Geom &, FieldPtrs<double>, const double[3], const double[3],

@@ -130,18 +130,26 @@ void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long 
 template <typename R>
 void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s);
 // e += dt curl b + scale * Js with the smoothed compact current Js (3 planes of
-// nx*ny*nz doubles, in the units of the path's current), and zeroing of Jzero
-template <typename R, typename ZT>
-void launch_e_advance_smoothed(const Geom &g, FieldPtrs<R> f, const double *Js, double scale, ZT *const Jzero[3],
+// nx*ny*nz values: double in the FP64 path, int64 fixed point in the mixed
+// path, in the units of the path's current), and zeroing of Jzero
+template <typename R, typename ZT, typename CT>
+void launch_e_advance_smoothed(const Geom &g, FieldPtrs<R> f, const CT *Js, double scale, ZT *const Jzero[3],
                                R dt, long long *hist_inc, cudaStream_t s);
 
 // smooth.cu: current smoothing (App. A.3.4).  Compact arrays are indexed
 // (k*ny + j)*nx + i over the interior, plane after plane.
+// Value type of a smoothed current: int64 fixed point for the mixed path's
+// current (unsigned long long storage), double for the FP64 path.
+template <typename JT> struct SmoothValue;
+template <> struct SmoothValue<unsigned long long> { typedef long long type; };
+template <> struct SmoothValue<double> { typedef double type; };
 // Smooths the deposited current J (padded planes; its ghost images are folded
 // into the interior in place, so J is consumed) `passes` >= 1 times into the
 // compact buffers buf[0..1] (3 planes each); returns the buffer with the result.
 template <typename JT>
-const double *launch_smooth_current(const Geom &g, JT *const J[3], int passes, double *const buf[2], cudaStream_t s);
+const typename SmoothValue<JT>::type *launch_smooth_current(const Geom &g, JT *const J[3], int passes,
+                                                            typename SmoothValue<JT>::type *const buf[2],
+                                                            cudaStream_t s);
 // one smoothing pass of one compact plane, in -> out (distinct arrays)
 void launch_smooth(const Geom &g, const double *in, double *out, cudaStream_t s);
 
@@ -194,7 +202,7 @@ struct FieldRunF {
     long long *hist_inc;    // E_FX phase: step counter of the history, incremented once (nullable)
     double scale;           // |alpha| 2^-36
     int smooth;             // current smoothing passes (0: off); the E_FX phase then reads sbuf[smooth & 1]
-    double *sbuf[2];        // compact FP64 smoothing buffers, 3 planes of nx*ny*nz each
+    long long *sbuf[2];     // compact fixed-point smoothing buffers, 3 planes of nx*ny*nz each
 };
 enum { FIELD_B_HALF = 0, FIELD_NODE = 1, FIELD_E_FX = 2 };
 void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_prefix_dev, int nblocks, int nruns,

@@ -576,3 +576,42 @@ def test_magnetized_plasma_k0_modes_are_the_cold_cutoffs():
     assert abs(_spectral_peak(omega, S, omega > 0.2) - wr) <= 0.015
     assert abs(_spectral_peak(omega, S, omega < -0.2) + wl) <= 0.015
     assert abs(_spectral_peak(omega, Sz, omega > 0.2) - wp) <= 0.015
+
+
+# ---------------------------------------------------------------- filament-merging diagnostic (Sect. 3.3)
+
+def test_step_current_is_recovered_from_two_field_states():
+    """J = e^{t+dt} - e^t - dt curl b^{t+dt/2} returns exactly what the oracle's
+    step added to e (the identity of main-loop steps 6 and 12)."""
+    from oracle import filaments
+    shape = (10, 9, 8)
+    arr = synth.random_state_arrays(61, 3, *shape, ppc=4, spread=1.5, amp_e=0.02, amp_b=0.02, colocate=False)
+    st = oracle.State.empty(3, *shape, dt=0.5, n_x=2.0, rho_sp0=8.0)
+    st.e[:] = arr["e"]
+    st.b[:] = arr["b"]
+    for s in arr["species"]:
+        st.species.append(oracle.Species(s["pos"], s["u"], s["q_over_e"], s["m_over_me"]))
+    e0 = st.e.copy()
+    J = oracle.step(st)
+    rec = filaments.step_current(e0, st.e, st.b, st.dt)
+    assert np.abs(rec - J).max() <= 1e-14 * max(1.0, np.abs(st.e).max())
+    assert np.abs(J).max() > 1e-4
+
+
+def test_filament_scale_of_gaussian_filaments_is_the_closed_form():
+    """Randomly placed Gaussian filaments exp(-r^2 / 2 s^2): the autocorrelation
+    of the field is exp(-r^2 / 4 s^2), so corr = 0.8 at r = 2 s sqrt(ln 1.25)
+    and the scale is 5 times that."""
+    from oracle import filaments
+    rng = np.random.default_rng(7)
+    n, s = 256, 3.0
+    y, x = np.mgrid[0:n, 0:n]
+    amp = np.zeros((n, n))
+    for cx, cy in rng.uniform(0, n, size=(600, 2)):
+        dx = np.minimum(np.abs(x - cx), n - np.abs(x - cx))
+        dy = np.minimum(np.abs(y - cy), n - np.abs(y - cy))
+        amp += np.exp(-(dx * dx + dy * dy) / (2 * s * s))
+    cur = np.zeros((3, 4, n, n))
+    cur[2] = amp[None]                         # J_z filaments, constant along z
+    expect = 5.0 * 2.0 * s * np.sqrt(np.log(1.25))
+    assert abs(filaments.filament_scale(cur) / expect - 1) <= 0.05
