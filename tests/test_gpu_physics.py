@@ -348,3 +348,128 @@ def test_magnetized_cold_modes_match_theory_and_table(precision, wce):
     assert abs(wp_m - wp) <= 0.015, (wp_m, wp)
     row = _cold_table()[wce]
     assert abs(wp_m - row[1]) <= 0.025 and abs(wl_m - row[2]) <= 0.025 and abs(wr_m - row[3]) <= 0.025, row
+
+
+# ---------------------------------------------------------------- 3D filamentation and filament merging (Sect. 3.2, 3.3)
+
+def filamentation_3d(precision=pic.PIC_MIXED, n_x=20.0, box_de=(4.5, 4.5, 15.0), rho_sp=80, beta0=0.995,
+                     theta=0.01, n_t=250, periods=7.0, snap_every=0.5):
+    """The paper's 3D counter-streaming setup: two electron-positron beams along
+    +-z (co-located pairs, so rho = 0), thermal spread theta = 0.01 (v_th = 0.1 c)
+    in each beam's frame, n_x cells per c/omega_pe, rho_sp superparticles per
+    cell in all, n_t steps per plasma period.  Returns (t / T_pe per step, total
+    magnetic energy per step, [(t / T_pe, filament scale in cells)])."""
+    from oracle import filaments
+    nx, ny, nz = (int(round(b * n_x)) for b in box_de)
+    ppc = rho_sp // 4
+    n = ppc * nx * ny * nz
+    dt = 2 * np.pi * n_x / n_t
+    d = pic.run_desc(3, nx, ny, nz, n_x, float(rho_sp), dt, [(-1.0, 1.0, n), (1.0, 1.0, n), (-1.0, 1.0, n),
+                                                              (1.0, 1.0, n)])
+    nsteps = int(round(periods * n_t))
+    snap = int(round(snap_every * n_t))
+    scales = []
+    with pic.Context([d], precision=precision) as ctx:
+        ctx.load_maxwell_juttner(0, 0, ppc, theta, (0.0, 0.0, beta0), seed=41)
+        ctx.load_maxwell_juttner(0, 1, ppc, theta, (0.0, 0.0, beta0), colocate_with=0, seed=42)
+        ctx.load_maxwell_juttner(0, 2, ppc, theta, (0.0, 0.0, -beta0), seed=43)
+        ctx.load_maxwell_juttner(0, 3, ppc, theta, (0.0, 0.0, -beta0), colocate_with=2, seed=44)
+        done = 0
+        while done + snap + 1 <= nsteps:
+            ctx.step(snap - 1)
+            f0 = ctx.get_state(0, fields_only=True)[0]
+            ctx.step(1)
+            f1 = ctx.get_state(0, fields_only=True)[0]
+            done += snap
+            J = filaments.step_current(f0[:3], f1[:3], f1[3:], dt)
+            scales.append((done / n_t, filaments.filament_scale(J)))
+        h = ctx.energy_history(0)
+    return np.arange(1, len(h) + 1) / n_t, h[:, 2], scales
+
+
+def _tau_total_energy(t, eb, window=0.5):
+    """e-folding time of the field amplitude, in T_pe, from the steepest fit of
+    ln E_B over a window of `window` T_pe: E_B ~ exp(2 t / tau)."""
+    dt = t[1] - t[0]
+    w = int(round(window / dt))
+    le = np.log(eb)
+    best = 0.0
+    for a in range(0, len(le) - w, max(1, w // 8)):
+        slope = np.polyfit(t[a:a + w], le[a:a + w], 1)[0]
+        best = max(best, slope)
+    return 2.0 / best
+
+
+def test_3d_relativistic_filamentation_matches_oracle_step_by_step():
+    """3D counter-streaming pair beams (beta0 = 0.995, Gamma0 = 10, theta =
+    0.01) in a 10 x 10 x 30 cell box (10 cells per c/omega_pe, 16 particles per
+    cell, 125 steps per plasma period), from the oracle loader's state, over 4
+    plasma periods: the magnetic energy grows by decades through the linear
+    phase.  The GPU's per-step magnetic energy at time t must match the
+    oracle's b^t (its b^{t-dt/2} advanced by the half step) to 1e-6 relative in
+    the FP64 path, and the mixed path's growth to 2 %."""
+    from oracle import mj
+    nx, ny, nz, n_x, n_t, ppc, beta0, theta = 10, 10, 30, 10.0, 125, 4, 0.995, 0.01
+    dt = 2 * np.pi * n_x / n_t
+    steps = 4 * n_t
+    n = ppc * nx * ny * nz
+    parts, sp = [], []
+    for s, (q, drift, seed) in enumerate([(-1.0, beta0, 51), (1.0, beta0, 52), (-1.0, -beta0, 53), (1.0, -beta0, 54)]):
+        pos, u = mj.load(seed, s, n, theta, (0.0, 0.0, drift), 3, nx, ny, nz)
+        if s % 2 == 1:
+            pos = parts[-1][:3].copy()          # co-located with the electrons of the same beam
+        parts.append(np.concatenate([pos, u]))
+        sp.append(q)
+    d = pic.run_desc(3, nx, ny, nz, n_x, 4.0 * ppc, dt, [(q, 1.0, n) for q in sp])
+    fields = np.zeros((6, nz, ny, nx))
+    st = oracle.State.empty(3, nx, ny, nz, dt, n_x, 4.0 * ppc)
+    for q, p in zip(sp, parts):   # copies: the oracle advances its particles in place
+        st.species.append(oracle.Species(p[:3].copy(), p[3:].copy(), q, 1.0))
+    eb_or = np.zeros(steps)
+    for k in range(steps):
+        b_save = st.b.copy()
+        oracle.b_advance(st, 0.5 * dt)                  # b^t of the step about to run
+        eb_or[k] = 0.5 * (st.b ** 2).sum() * st.inv_alpha_abs
+        st.b[:] = b_save
+        oracle.step(st)
+    hist = {}
+    for name, prec in (("fp64", pic.PIC_FP64), ("mixed", pic.PIC_MIXED)):
+        with pic.Context([d], precision=prec) as ctx:
+            ctx.set_state(0, fields, parts)
+            ctx.step(steps)
+            hist[name] = ctx.energy_history(0)[:, 2]
+    growth = eb_or[-1] / eb_or[n_t // 2]
+    assert growth > 1e3, growth
+    live = eb_or > 0
+    assert np.abs(hist["fp64"][live] / eb_or[live] - 1).max() <= 1e-6
+    t = np.arange(steps) / n_t
+    lin = (t > 1.0) & (t < 3.5)
+    s_or = np.polyfit(t[lin], np.log(eb_or[lin]), 1)[0]
+    s_mx = np.polyfit(t[lin], np.log(hist["mixed"][lin]), 1)[0]
+    assert abs(s_mx / s_or - 1) <= 0.02, (s_mx, s_or)
+
+
+def test_3d_filamentation_at_the_paper_scale_grows_and_its_filaments_merge():
+    """The 4.5 x 4.5 x 15 d_e setup of Table two_stream (beta0 = 0.995, 20 cells
+    per d_e, rho_sp = 80, 250 steps per plasma period; 90 x 90 x 300 cells, 194M
+    particles, ragged 8^3 tiles).  The magnetic energy grows exponentially and
+    saturates; its growth time lies between the cold maximum rate and 1.75
+    times it.  The filament scale (Sect. 3.3) grows through the non-linear
+    phase: at saturation it is more than three times its value at the middle of
+    the linear phase."""
+    t, eb, scales = filamentation_3d()
+    tau = _tau_total_energy(t[t > 0.5], eb[t > 0.5])
+    tau_th = theory.tau_filamentation_pair(0.995)
+    isat = int(np.argmax(eb))
+    print("3D filamentation: tau_tot %.3f T_pe (cold maximum %.3f), saturation at %.2f T_pe" % (tau, tau_th, t[isat]))
+    print("filament scale (T_pe, cells):", [(round(a, 2), round(b, 2)) for a, b in scales])
+    assert eb[isat] / eb[int(0.5 * 250)] > 1e3
+    assert tau_th <= tau <= 1.75 * tau_th, tau
+    # middle of the linear phase: halfway (in log E_B) between 0.5 T_pe and saturation
+    le = np.log(np.maximum(eb, 1e-300))
+    lo = le[int(0.5 * 250)]
+    tmid = t[int(np.argmax(le > 0.5 * (lo + le[isat])))]
+    s_mid = np.interp(tmid, [a for a, _ in scales], [b for _, b in scales])
+    s_sat = np.interp(t[isat], [a for a, _ in scales], [b for _, b in scales])
+    print("scale at %.2f T_pe: %.2f cells, at saturation: %.2f cells" % (tmid, s_mid, s_sat))
+    assert s_sat > 3.0 * s_mid
