@@ -473,3 +473,61 @@ def test_3d_filamentation_at_the_paper_scale_grows_and_its_filaments_merge():
     s_sat = np.interp(t[isat], [a for a, _ in scales], [b for _, b in scales])
     print("scale at %.2f T_pe: %.2f cells, at saturation: %.2f cells" % (tmid, s_mid, s_sat))
     assert s_sat > 3.0 * s_mid
+
+
+# ---------------------------------------------------------------- thermalization time against rho_sp (Sect. 5.2)
+
+def _half_thermalization_time(rho_sp, precision=pic.PIC_MIXED, n=25, n_x=25.0, n_t=500, mu=25.0, t_cold=1.6e-3,
+                              t_hot=1.8e-2, sample=0.5, progress=0.25, max_periods=120.0):
+    """Two ion-electron plasmas, cold (T = 1.6e-3 m_e c^2) and hot (1.8e-2), m_i/m_e
+    = 25, in a 25^3 box with 25 cells per c/omega_pe and 500 steps per plasma
+    period (the paper's setup), rho_sp superparticles per cell over the four
+    species.  Each plasma's ions sit on its electrons (rho = 0).  The cold
+    electrons' temperature T1 relaxes as T_inf - (T_inf - T1(0)) exp(-2 t / t_th),
+    T_inf = (T1 + T2) / 2 measured; t_th is taken from the slope of
+    ln(T_inf - T1) over the start of the relaxation (until T1 has covered
+    `progress` of the way), in plasma periods."""
+    ppc = rho_sp // 4
+    npart = ppc * n ** 3
+    dt = 2 * np.pi * n_x / n_t
+    d = pic.run_desc(3, n, n, n, n_x, float(rho_sp), dt, [(-1.0, 1.0, npart), (1.0, mu, npart),
+                                                          (-1.0, 1.0, npart), (1.0, mu, npart)])
+    ts, gap = [], []
+    every = int(round(sample * n_t))
+    with pic.Context([d], precision=precision) as ctx:
+        ctx.load_maxwell_juttner(0, 0, ppc, t_cold, seed=71)
+        ctx.load_maxwell_juttner(0, 1, ppc, t_cold / mu, colocate_with=0, seed=72)
+        ctx.load_maxwell_juttner(0, 2, ppc, t_hot, seed=73)
+        ctx.load_maxwell_juttner(0, 3, ppc, t_hot / mu, colocate_with=2, seed=74)
+        t = 0.0
+        while t < max_periods:
+            dg = ctx.diagnostics(0)
+            t1, t2 = dg["temperature"][0], dg["temperature"][2]
+            ts.append(t)
+            gap.append(0.5 * (t2 - t1))          # T_inf - T1
+            if gap[-1] <= (1.0 - progress) * gap[0]:
+                break
+            ctx.step(every)
+            t += sample
+    ts, gap = np.array(ts), np.array(gap)
+    slope = np.polyfit(ts, np.log(gap), 1)[0]
+    return -2.0 / slope, ts[-1]
+
+
+def test_thermalization_time_grows_as_rho_sp():
+    """Sect. 5.2: the collision- and fluctuation-induced thermalization time of
+    a PIC plasma scales as the PIC plasma parameter, t_th ~ rho_sp at fixed
+    resolution (the paper disclaims the constant).  rho_sp = 4, 16, 64, 128:
+    the log-log slope of t_th against rho_sp must lie in [0.7, 1.3]."""
+    res = {r: _half_thermalization_time(r) for r in (4, 16, 64, 128)}
+    print("thermalization time t_th / T_pe (window):", {r: (round(v[0], 1), v[1]) for r, v in res.items()})
+    r = np.array(sorted(res))
+    tth = np.array([res[k][0] for k in r])
+    slope = np.polyfit(np.log(r), np.log(tth), 1)[0]
+    print("log-log slope %.3f" % slope)
+    assert np.all(np.diff(tth) > 0)
+    assert 0.7 <= slope <= 1.3, slope
+    # the FP64 path relaxes at the same rate: the mixed arithmetic does not change the collisionality
+    t64 = _half_thermalization_time(4, precision=pic.PIC_FP64)[0]
+    print("rho_sp = 4: t_th %.1f (mixed) %.1f (FP64)" % (res[4][0], t64))
+    assert abs(t64 / res[4][0] - 1) <= 0.2
