@@ -230,6 +230,9 @@ def run_ours(args, w):
         torch.cuda.synchronize()
 
     seed = replica_seed(rank)
+    # measured FMA throughput, the ALU denominators (the FP64 path is bound by the FP64 pipe)
+    alu = {"fp32_fma_tflops": pic.alu_peak(pic.PIC_PEAK_FP32_FMA),
+           "fp64_fma_tflops": pic.alu_peak(pic.PIC_PEAK_FP64_FMA)}
     if w.get("ensemble"):
         members = ensemble_members(w["ensemble"])
         descs = []
@@ -332,7 +335,7 @@ def run_ours(args, w):
         e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     if args.no_fp64:
         results["fp64"] = None
-    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, len(descs))
+    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, len(descs), alu)
 
 
 def _e2e(pic, torch, desc, w, seed, args, barrier):
@@ -366,10 +369,33 @@ def _e2e(pic, torch, desc, w, seed, args, barrier):
 # ncu capture of the same kernel and tiling on the 64^3 case (profiles/
 # push_mixed_thermal3d_64.md: 917.4 MB for 16,777,216 particles), scaled to a
 # launch by the particles it processes.  None where no capture exists.
+# FP64 path: particle state read + written per particle-step (x, u as doubles)
+FP64_BYTES_PER_PARTICLE = {2: 80.0, 3: 96.0}
+# FP64 flops per particle-step of k_push_fp64 (dadd + dmul + 2 dfma, ncu instruction
+# counts on the 64^3 and 512^2 thermal workloads divided by the particles pushed)
+FP64_FLOPS_PER_PARTICLE = {}
 PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.4e6 / 16777216}
 
 
-def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1):
+def _fp64_roofline(w, f64, npart, alu, peak_hbm):
+    """The FP64 path's push against the measured FP64 FMA peak: FP64 flops per
+    particle-step from ncu instruction counts of k_push_fp64 (dadd + dmul +
+    2 dfma), times the particles, over the push time per step (CUDA events)."""
+    if f64 is None or f64["push_n"] == 0:
+        return None
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": alu["fp64_fma_tflops"], "peak_kind": "measured (pic_alu_peak)",
+           "push_ms_per_step": f64["push_ms"] / f64["steps"],
+           "hbm_frac": (FP64_BYTES_PER_PARTICLE[w["ndim"]] * npart / (f64["push_ms"] / f64["steps"] * 1e-3) / 1e9
+                        / peak_hbm)}
+    flops = FP64_FLOPS_PER_PARTICLE.get(w["ndim"])
+    if flops is not None:
+        ach = flops * npart / (f64["push_ms"] / f64["steps"] * 1e-3) / 1e12
+        out.update(achieved=ach, frac=ach / alu["fp64_fma_tflops"], flops_per_particle_step=flops,
+                   flops_source="ncu FP64 instruction counts of k_push_fp64 (dadd + dmul + 2 dfma)")
+    return out
+
+
+def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1, alu=None):
     m = results["mixed"]
     value = job_value(npart, m["steps"], m["ms"], world)
     f64 = results["fp64"]
@@ -388,7 +414,9 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                        "tuning": m["tuning"]},
             "fp64": None if f64 is None else {"value": npart * f64["steps"] / (f64["ms"] * 1e6) * world,
                                               "unit": "particle-steps/ns", "ms_per_step": f64["ms"] / f64["steps"],
-                                              "steps": f64["steps"]},
+                                              "steps": f64["steps"],
+                                              "roofline": _fp64_roofline(w, f64, npart, alu, peak)},
+            "alu_peaks": alu,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (PUSH_TRAFFIC_B_PER_PARTICLE.get(w.get("ndim"), 0.0) * npart
                                      if w.get("ndim") in PUSH_TRAFFIC_B_PER_PARTICLE and nruns == 1 else None),

@@ -347,6 +347,20 @@ pic_status pic_gauss_residual_static(int ndim, int nx, int ny, int nz, const dou
                                      const int64_t *counts, const double *const *pos, const double *alpha,
                                      double *out, void *stream);
 
+/* Measured fused multiply-add throughput of the current device, the ALU
+ * denominators of the rooflines (the FP64 path is bound by the FP64 pipe).
+ *  kind    PIC_PEAK_FP32_FMA or PIC_PEAK_FP64_FMA
+ *  tflops  out: TFLOP/s, 2 flops per FMA, from CUDA events around one launch of
+ *          8 blocks of 256 threads per SM, each thread running 8 independent
+ *          FMA chains (after one warm-up launch)
+ *  ms      out (nullable): duration of the timed launch
+ * Needs no context; allocates and frees a few bytes of device memory;
+ * synchronous on the legacy default stream (about 20 ms).  Returns PIC_EINVAL
+ * for an unknown kind or a null tflops, PIC_ECUDA when a CUDA call fails. */
+#define PIC_PEAK_FP32_FMA 0
+#define PIC_PEAK_FP64_FMA 1
+pic_status pic_alu_peak(int kind, double *tflops, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

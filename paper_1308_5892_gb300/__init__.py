@@ -28,7 +28,7 @@ ABI_FUNCTIONS = [
     "pic_abi_version", "pic_init", "pic_destroy", "pic_last_error", "pic_set_state", "pic_get_state",
     "pic_set_uniform_field", "pic_load_maxwell_juttner", "pic_step", "pic_sync", "pic_diagnostics",
     "pic_energy_history", "pic_get_tuning", "pic_get_counters", "pic_kernel_time", "pic_get_particles",
-    "pic_mlp_train", "pic_mlp_set_weights", "pic_mlp_get_weights", "pic_mlp_gradients", "pic_mlp_infer",
+    "pic_alu_peak", "pic_mlp_train", "pic_mlp_set_weights", "pic_mlp_get_weights", "pic_mlp_gradients", "pic_mlp_infer",
     "pic_mj_sample_marginal", "pic_gauss_residual_static", "pic_autotune", "pic_set_flags",
 ]
 MLP_PARAMS = 8641
@@ -131,6 +131,7 @@ def lib(build_if_missing=True):
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)], st),
         "pic_autotune": ([P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_int)], st),
+        "pic_alu_peak": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], st),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -155,6 +156,19 @@ def run_desc(ndim, nx, ny, nz, n_x, rho_sp0, dt, species, bc=(0, 0, 0), smooth_p
         d.species[k].m_over_me = m
         d.species[k].capacity = int(cap)
     return d
+
+
+PIC_PEAK_FP32_FMA, PIC_PEAK_FP64_FMA = 0, 1
+
+
+def alu_peak(kind):
+    """Measured FMA throughput of the current device in TFLOP/s (pic_alu_peak)."""
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    st = lib().pic_alu_peak(kind, ctypes.byref(tf), ctypes.byref(ms))
+    if st != PIC_OK:
+        raise PicError(st, "pic_alu_peak failed")
+    return tf.value
 
 
 def _dptr(a):
