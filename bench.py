@@ -371,9 +371,14 @@ def _e2e(pic, torch, desc, w, seed, args, barrier):
 # launch by the particles it processes.  None where no capture exists.
 # FP64 path: particle state read + written per particle-step (x, u as doubles)
 FP64_BYTES_PER_PARTICLE = {2: 80.0, 3: 96.0}
-# FP64 flops per particle-step of k_push_fp64 (dadd + dmul + 2 dfma, ncu instruction
-# counts on the 64^3 and 512^2 thermal workloads divided by the particles pushed)
-FP64_FLOPS_PER_PARTICLE = {}
+# FP64 flops per particle-step of k_push_fp64 (dadd + dmul + 2 dfma) and FP64
+# instructions (dadd + dmul + dfma), from ncu instruction counts on the 64^3 and 512^2
+# thermal workloads divided by the particles pushed: 3D 108 + 80 + 86, 2D 58 + 50 + 62
+FP64_FLOPS_PER_PARTICLE = {3: 360.0, 2: 232.0}
+FP64_INST_PER_PARTICLE = {3: 274.0, 2: 170.0}
+# FP32 flops per particle-step of the mixed 3D push (fadd + fmul + 2 ffma: 32.4 + 92.8 +
+# 103.3 per particle, ncu on the 64^3 workload)
+MIXED_FP32_FLOPS_PER_PARTICLE = {3: 331.8}
 PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.4e6 / 16777216}
 
 
@@ -390,8 +395,10 @@ def _fp64_roofline(w, f64, npart, alu, peak_hbm):
     flops = FP64_FLOPS_PER_PARTICLE.get(w["ndim"])
     if flops is not None:
         ach = flops * npart / (f64["push_ms"] / f64["steps"] * 1e-3) / 1e12
+        inst = FP64_INST_PER_PARTICLE[w["ndim"]] * npart / (f64["push_ms"] / f64["steps"] * 1e-3) / 1e12
         out.update(achieved=ach, frac=ach / alu["fp64_fma_tflops"], flops_per_particle_step=flops,
-                   flops_source="ncu FP64 instruction counts of k_push_fp64 (dadd + dmul + 2 dfma)")
+                   flops_source="ncu FP64 instruction counts of k_push_fp64 (dadd + dmul + 2 dfma)",
+                   fp64_pipe_frac=inst / (0.5 * alu["fp64_fma_tflops"]))
     return out
 
 
@@ -426,7 +433,11 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                          "field_ms_per_step": m["field_ms"] / m["steps"], "sort_ms_total": m["sort_ms"],
                          "sort_interval": m["tuning"]["sort_interval"],
                          "ms_per_step_direct_launches": m["ms_direct"] / m["steps"],
-                         "sorts_timed": -(-m["steps"] // m["tuning"]["sort_interval"])},
+                         "sorts_timed": -(-m["steps"] // m["tuning"]["sort_interval"]),
+                         "fp32_frac": (MIXED_FP32_FLOPS_PER_PARTICLE[w["ndim"]] * npart / (push_launch_ms * 1e-3)
+                                       / 1e12 / alu["fp32_fma_tflops"]
+                                       if alu and w.get("ndim") in MIXED_FP32_FLOPS_PER_PARTICLE and nruns == 1
+                                       else None)},
             "cpu_baseline": None,
             "e2e": None if e2e_s is None else {
                 "value": npart * args.steps / (e2e_s * 1e9) * world, "unit": "particle-steps/ns",
