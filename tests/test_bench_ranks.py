@@ -55,3 +55,38 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_report_line_carries_the_contract_keys():
+    """The JSON line of bench.py (built from timings, here synthetic) holds the
+    contract's keys and the roofline objects, including the ALU rooflines and
+    the smoothing leg, without a GPU."""
+    import contextlib
+    import io
+    import json
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    args = types.SimpleNamespace(steps=20, warmup=3, no_cpu_baseline=True, smooth=1, gpus=1)
+    w = dict(bench.WORKLOADS["thermal3d_128"], smooth=1)
+    common = dict(ms_direct=160.0, field_ms=7.0, smooth_ms=1.3, ncell=128 ** 3, clocks={"sm_mhz": 2070.0},
+                  diag={"gauss_max": 1e-6, "rho_max": 1.5})
+    mixed = dict(common, ms=160.0, steps=20, push_ms=120.0, push_n=20, sort_ms=30.0,
+                 counters={"bytes_per_particle_step": 56.0, "launches_per_step": 9.0},
+                 tuning={"tile": [8, 8, 8], "sort_interval": 3, "halo": 3})
+    fp64 = dict(common, ms=1300.0, steps=5, push_ms=1290.0, push_n=5, sort_ms=0.0,
+                counters={"bytes_per_particle_step": 96.0, "launches_per_step": 5.0}, tuning=None)
+    alu = {"fp32_fma_tflops": 78.3, "fp64_fma_tflops": 1.25}
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench._report(args, w, {"mixed": mixed, "fp64": fp64}, 134217728, 1, 0, 3.0, 6.5e9, 6.5e9, None, 1, alu)
+    d = json.loads(buf.getvalue())
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        assert k in d, k
+    r = d["roofline"]
+    assert r["bound"] == "hbm" and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(d["value"] - 134217728 * 20 / (160.0 * 1e6)) < 1e-9
+    assert d["fp64"]["roofline"]["bound"] == "alu" and 0 < d["fp64"]["roofline"]["frac"] < 1
+    assert 0 < r["fp32_frac"] < 1 and 0 < r["smooth"]["frac"] < 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 6.5e9 / 20
