@@ -365,10 +365,6 @@ def _e2e(pic, torch, desc, w, seed, args, barrier):
     return e2e_s, nbytes, nbytes
 
 
-# DRAM bytes (read + written) per particle-step of the 3D push kernel, from one
-# ncu capture of the same kernel and tiling on the 64^3 case (profiles/
-# push_mixed_thermal3d_64.md: 917.4 MB for 16,777,216 particles), scaled to a
-# launch by the particles it processes.  None where no capture exists.
 # FP64 path: particle state read + written per particle-step (x, u as doubles)
 FP64_BYTES_PER_PARTICLE = {2: 80.0, 3: 96.0}
 # FP64 flops per particle-step of k_push_fp64 (dadd + dmul + 2 dfma) and FP64
@@ -379,6 +375,10 @@ FP64_INST_PER_PARTICLE = {3: 274.0, 2: 170.0}
 # FP32 flops per particle-step of the mixed 3D push (fadd + fmul + 2 ffma: 32.4 + 92.8 +
 # 103.3 per particle, ncu on the 64^3 workload)
 MIXED_FP32_FLOPS_PER_PARTICLE = {3: 331.8}
+# DRAM bytes (read + written) per particle-step of the 3D push kernel, from one
+# ncu capture of the same kernel and tiling on the 64^3 case (profiles/
+# push_mixed_thermal3d_64.md: 917.4 MB for 16,777,216 particles), scaled to a
+# launch by the particles it processes.  None where no capture exists.
 PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.4e6 / 16777216}
 
 

@@ -194,11 +194,15 @@ const char *pic_last_error(const pic_ctx *ctx);
  * is checked on the device while it is converted: a non-finite value gives
  * PIC_ENUMERIC and a position outside the domain PIC_EINVAL, after which the
  * run's state is undefined until the next successful pic_set_state or load.
- * Host buffers are read during the call only; pinned buffers are copied by DMA. */
+ * Host buffers are read during the call only.  A buffer that lies inside one
+ * page-locked allocation (cudaHostAlloc, cudaHostRegister) is read by the
+ * conversion kernels directly over the host link; other buffers are staged
+ * through device memory.  Both give the same state. */
 pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in);
 
 /* Download the state into caller buffers (converted to FP64).  A NULL
- * particles[s] skips species s (count[s] still receives its size). */
+ * particles[s] skips species s (count[s] still receives its size).  As for
+ * pic_set_state, page-locked buffers are written by the kernels directly. */
 pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out);
 
 /* Copy chosen particles of one species by id (ids as returned in load/set

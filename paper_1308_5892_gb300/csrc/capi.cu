@@ -259,14 +259,15 @@ __global__ void k_unpad_field(Geom g, const R *src, double *dst) {
     }
 }
 
-// staging: 6 planes of m doubles (x, y, z, ux, uy, uz) for ids [a, a+m)
-__global__ void k_upload_mixed(Geom g, const double *st, long long m, long long a, SpeciesMixed d, int *err) {
+// st: 6 planes (x, y, z, ux, uy, uz) `stride` doubles apart, values for ids [a, a+m)
+__global__ void k_upload_mixed(Geom g, const double *st, long long stride, long long m, long long a, SpeciesMixed d,
+                               int *err) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
         int c[3] = {0, 0, 0};
         float o[3] = {0.f, 0.f, 0.f};
         const int n3[3] = {g.nx, g.ny, g.nz};
         for (int ax = 0; ax < g.ndim; ++ax) {
-            const double x = st[ax * m + q];
+            const double x = st[ax * stride + q];
             if (!isfinite(x) || !in_domain(g, ax, x)) {
                 atomicOr(err, isfinite(x) ? ERR_RANGE : ERR_NONFINITE);
                 continue;   // the state is rejected; keep the stored cell in range
@@ -281,14 +282,14 @@ __global__ void k_upload_mixed(Geom g, const double *st, long long m, long long 
             o[ax] = off;
         }
         for (int comp = 3; comp < 6; ++comp)
-            if (!isfinite(st[comp * m + q])) atomicOr(err, ERR_NONFINITE);
+            if (!isfinite(st[comp * stride + q])) atomicOr(err, ERR_NONFINITE);
         d.cell[a + q] = pack_cell(g.ndim, c[0], c[1], c[2]);
         d.off[0][a + q] = o[0];
         d.off[1][a + q] = o[1];
         if (g.ndim == 3) d.off[2][a + q] = o[2];
-        d.u[0][a + q] = (float)st[3 * m + q];
-        d.u[1][a + q] = (float)st[4 * m + q];
-        d.u[2][a + q] = (float)st[5 * m + q];
+        d.u[0][a + q] = (float)st[3 * stride + q];
+        d.u[1][a + q] = (float)st[4 * stride + q];
+        d.u[2][a + q] = (float)st[5 * stride + q];
         d.id[a + q] = (int32_t)(a + q);
     }
 }
@@ -325,17 +326,19 @@ __global__ void k_pick64(Species64 s, const long long *ids, long long m, int ndi
 
 // Download of ids [a, a+m) through the id -> storage index map inv: coalesced
 // staging writes, one pass over the chunk's own particles.
-__global__ void k_download_by_id(Geom g, SpeciesMixed s, const int *inv, long long a, long long m, double *st) {
+// st: 6 planes `stride` doubles apart, written for ids [a, a+m)
+__global__ void k_download_by_id(Geom g, SpeciesMixed s, const int *inv, long long a, long long m, double *st,
+                                 long long stride) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
         const int p = inv[a + q];
         int i, j, k;
         unpack_cell(g.ndim, s.cell[p], i, j, k);
         st[q] = (double)i + (double)s.off[0][p];
-        st[m + q] = (double)j + (double)s.off[1][p];
-        st[2 * m + q] = g.ndim == 3 ? (double)k + (double)s.off[2][p] : 0.0;
-        st[3 * m + q] = s.u[0][p];
-        st[4 * m + q] = s.u[1][p];
-        st[5 * m + q] = s.u[2][p];
+        st[stride + q] = (double)j + (double)s.off[1][p];
+        st[2 * stride + q] = g.ndim == 3 ? (double)k + (double)s.off[2][p] : 0.0;
+        st[3 * stride + q] = s.u[0][p];
+        st[4 * stride + q] = s.u[1][p];
+        st[5 * stride + q] = s.u[2][p];
     }
 }
 
@@ -460,6 +463,50 @@ EncodeTiledFn encode_tiled() {
             cudaGetLastError();
     }
     return fn;
+}
+
+// cuPointerGetAttribute through the same entry point.
+typedef CUresult (*PointerAttrFn)(void *, CUpointer_attribute, CUdeviceptr);
+PointerAttrFn pointer_attr() {
+    static PointerAttrFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (PointerAttrFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// The host buffer [p, p + bytes) when it lies inside one page-locked allocation
+// that the device addresses at the same virtual address (pinned memory under
+// unified addressing), so that kernels can read or write it directly over the
+// host link; nullptr otherwise (pageable memory, or a range that leaves the
+// allocation), in which case the caller stages through device memory.
+template <typename T>
+T *mapped_host(T *p, size_t bytes) {
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer != (const void *)p) return nullptr;
+    PointerAttrFn f = pointer_attr();
+    if (!f) return nullptr;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (f(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)p) != CUDA_SUCCESS ||
+        f(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)p) != CUDA_SUCCESS)
+        return nullptr;
+    const uintptr_t a = (uintptr_t)p;
+    if (a < (uintptr_t)start || a + bytes > (uintptr_t)start + size) return nullptr;
+    return p;
 }
 
 // TMA descriptors of the node-field arrays with a box of one tile + halo.  The
@@ -1231,13 +1278,15 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
     }
     if (ctx->precision == PIC_MIXED && (st = io_ready(ctx)) != PIC_OK) return st;
     double *stg = (double *)ctx->staging;
-    const size_t rs = real_size(ctx);
+    // page-locked host buffers are read by the conversion kernels directly
+    const double *fmap = mapped_host(in->fields, sizeof(double) * 6 * ncell);
     for (int c = 0; c < 6; ++c) {
-        CK(cudaMemcpyAsync(stg, in->fields + c * ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, sm));
+        const double *src = fmap ? fmap + c * ncell : stg;
+        if (!fmap) CK(cudaMemcpyAsync(stg, in->fields + c * ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, sm));
         if (ctx->precision == PIC_FP64)
-            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (double *)r.F + c * g.pcells, ctx->d_err);
+            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, src, (double *)r.F + c * g.pcells, ctx->d_err);
         else
-            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, stg, (float *)r.F + c * g.pcells, ctx->d_err);
+            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, src, (float *)r.F + c * g.pcells, ctx->d_err);
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(r.J, 0, 6 * 8 * g.pcells, sm));
@@ -1259,6 +1308,11 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
             S.cur = 0;
             S.tiled = false;
             S.counted = false;
+            if (const double *Pm = mapped_host(P, sizeof(double) * 6 * (size_t)n)) {
+                k_upload_mixed<<<nblk(n), 256, 0, sm>>>(g, Pm, n, n, 0, S.mb[0], ctx->d_err);
+                CK(cudaGetLastError());
+                continue;
+            }
             // chunk c is copied into half c % 2 on the transfer stream while the
             // previous chunk is converted on the context stream
             const size_t half = (ctx->staging_bytes / 2) & ~size_t(255);
@@ -1279,7 +1333,7 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
                 }
                 CK(cudaEventRecord(ctx->io_ev[1 + b], io));
                 CK(cudaStreamWaitEvent(sm, ctx->io_ev[1 + b], 0));
-                k_upload_mixed<<<nblk(m), 256, 0, sm>>>(g, hb[b], m, a0, S.mb[0], ctx->d_err);
+                k_upload_mixed<<<nblk(m), 256, 0, sm>>>(g, hb[b], m, m, a0, S.mb[0], ctx->d_err);
                 CK(cudaGetLastError());
                 CK(cudaEventRecord(ctx->io_ev[3 + b], sm));
                 used[b] = true;
@@ -1310,12 +1364,16 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
     }
     cudaStream_t sm = ctx->stream;
     double *stg = (double *)ctx->staging;
+    // page-locked host buffers are written by the conversion kernels directly
+    double *fmap = mapped_host(out->fields, sizeof(double) * 6 * ncell);
     for (int c = 0; c < 6; ++c) {
+        double *dst = fmap ? fmap + c * ncell : stg;
         if (ctx->precision == PIC_FP64)
-            k_unpad_field<double><<<nblk(ncell), 256, 0, sm>>>(g, (double *)r.F + c * g.pcells, stg);
+            k_unpad_field<double><<<nblk(ncell), 256, 0, sm>>>(g, (double *)r.F + c * g.pcells, dst);
         else
-            k_unpad_field<float><<<nblk(ncell), 256, 0, sm>>>(g, (float *)r.F + c * g.pcells, stg);
-        CK(cudaMemcpyAsync(out->fields + c * ncell, stg, sizeof(double) * ncell, cudaMemcpyDeviceToHost, sm));
+            k_unpad_field<float><<<nblk(ncell), 256, 0, sm>>>(g, (float *)r.F + c * g.pcells, dst);
+        if (!fmap)
+            CK(cudaMemcpyAsync(out->fields + c * ncell, stg, sizeof(double) * ncell, cudaMemcpyDeviceToHost, sm));
     }
     for (int s = 0; s < r.d.nspecies; ++s) {
         SpeciesState &S = r.sp[s];
@@ -1334,10 +1392,15 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
             // its own measured slower here than this serial form); the id -> storage
             // index map lets each chunk touch only its own particles
             k_id_index<<<nblk(n), 256, 0, sm>>>(S.mb[S.cur].id, n, r.perm);
+            if (double *Pm = mapped_host(P, sizeof(double) * 6 * (size_t)n)) {
+                k_download_by_id<<<nblk(n), 256, 0, sm>>>(g, S.mb[S.cur], r.perm, 0, n, Pm, n);
+                CK(cudaGetLastError());
+                continue;
+            }
             const int64_t chunk = (int64_t)(ctx->staging_bytes / (6 * sizeof(double)));
             for (int64_t a0 = 0; a0 < n; a0 += chunk) {
                 const int64_t m = std::min(chunk, n - a0);
-                k_download_by_id<<<nblk(m), 256, 0, sm>>>(g, S.mb[S.cur], r.perm, a0, m, stg);
+                k_download_by_id<<<nblk(m), 256, 0, sm>>>(g, S.mb[S.cur], r.perm, a0, m, stg, m);
                 CK(cudaGetLastError());
                 for (int a = 0; a < 6; ++a)
                     CK(cudaMemcpyAsync(P + a * n + a0, stg + a * m, sizeof(double) * m, cudaMemcpyDeviceToHost, sm));

@@ -266,3 +266,36 @@ def test_mixed_energy_history_tracks_oracle():
     ek_plus = sum(sp.m_over_me * (np.sqrt(1 + (sp.u ** 2).sum(0)) - 1).sum() for sp in st.species)
     assert np.isclose(hist[0, 0], 0.5 * (ek_minus + ek_plus), rtol=1e-5)
     assert np.all(np.isfinite(hist))
+
+
+@pytest.mark.parametrize("precision", [pic.PIC_MIXED, pic.PIC_FP64])
+def test_state_transfer_through_page_locked_buffers_equals_pageable(precision):
+    """Page-locked host buffers are read and written by the conversion kernels
+    directly; the transfers are bitwise those of the staged transfer of
+    pageable buffers, and a bad value is still rejected.  After steps the mixed
+    path stays bitwise equal (exact current); the FP64 path's global FP64
+    atomics sum in a varying order, so two contexts agree to round-off."""
+    torch = pytest.importorskip("torch")
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    desc, fields, parts, arr = _make(3, (20, 16, 12), 4, seed=77, spread=1.0, amp=0.05, colocate=False)
+    with pic.Context([desc], precision=precision) as a, pic.Context([desc], precision=precision) as b:
+        a.set_state(0, fields, parts)
+        b.set_state(0, pin(fields), [pin(p) for p in parts])
+        for nsteps in (0, 3):
+            a.step(nsteps)
+            b.step(nsteps)
+            fa, pa, _ = a.get_state(0)
+            out_f = pin(np.zeros_like(fa))
+            out_p = [pin(np.zeros_like(p)) for p in pa]
+            fb, pb, _ = b.get_state(0, out=(out_f, out_p))
+            exact = nsteps == 0 or precision == pic.PIC_MIXED
+            for x, y in [(fa, fb)] + list(zip(pa, pb)):
+                if exact:
+                    assert np.array_equal(x, y)
+                else:
+                    assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(y).max())
+        bad = [pin(p) for p in parts]
+        bad[0][4, 5] = np.inf
+        with pytest.raises(pic.PicError) as e:
+            b.set_state(0, pin(fields), bad)
+        assert e.value.status == pic.PIC_ENUMERIC
