@@ -9,6 +9,17 @@
   two-fluid limit, delta^2 = sum_s omega_ps^2 beta_s^2 / gamma_s over the beam
   populations, gives tau = (1/2 pi) sqrt(Gamma0) / beta0 T_pe for two electron
   beams of half density each on a positron background at rest.
+- Unmagnetized thermal modes (Sect. 3.1.1): the transverse electromagnetic
+  wave omega^2 = omega_P^2 + k^2 c^2 and the Langmuir wave
+  omega^2 = omega_P^2 (1 + 3 k^2 lambda_D^2), lambda_D = v_th / omega_pe, with
+  omega_P = omega_pe (1 + m_e/m_i)^1/2.
+- k = 0 pulsations of a cold magnetized electron-ion plasma (Sect. 3.1.2):
+  omega_P along B0, and the cut-offs omega_L, omega_R across it.  With
+  infinitely heavy ions omega_{L,R} = [(omega_ce^2 + 4 omega_pe^2)^1/2 -/+
+  omega_ce] / 2 (the paper's formulas).  With mobile ions they are the
+  positive roots of the cold-plasma conditions L(omega) = 0 and R(omega) = 0,
+  R = 1 - sum_s omega_ps^2 / (omega (omega + Omega_s)), L(omega) = R(-omega),
+  Omega_s = q_s B / m_s signed, omega_pi^2 = omega_pe^2 m_e / m_i.
 """
 import numpy as np
 
@@ -52,3 +63,13 @@ def cold_cutoffs_two_species(wce, mass_ratio):
              - np.poly1d([1.0, -wce]) / mass_ratio)
     roots = np.sort(cubic.roots.real)
     return -roots[0], roots[-1]
+
+
+def transverse_wave(kc, mass_ratio):
+    """omega / omega_pe of the transverse wave at wavenumber kc = k c / omega_pe."""
+    return np.sqrt(1.0 + 1.0 / mass_ratio + kc * kc)
+
+
+def langmuir_wave(k_lambda, mass_ratio):
+    """omega / omega_pe of the thermal Langmuir wave at k lambda_D (lambda_D = v_th/omega_pe)."""
+    return np.sqrt((1.0 + 1.0 / mass_ratio) * (1.0 + 3.0 * k_lambda * k_lambda))

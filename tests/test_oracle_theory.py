@@ -56,3 +56,14 @@ def test_two_species_cutoffs_tend_to_the_heavy_ion_formulas():
         R = 1 - 1 / (wr * (wr - wce)) - (1 / mu) / (wr * (wr + wce / mu))
         L = 1 - 1 / (wl * (wl + wce)) - (1 / mu) / (wl * (wl - wce / mu))
         assert abs(R) < 1e-10 and abs(L) < 1e-10
+
+
+def test_thermal_mode_branches_meet_at_the_plasma_frequency():
+    """Sect. 3.1.1: both unmagnetized branches start at omega_P (1.010 omega_pe for
+    m_i/m_e = 49, as printed), the Langmuir branch rises as 3 k^2 lambda_D^2 / 2
+    at small k, and the transverse branch tends to the light line k c."""
+    assert abs(theory.transverse_wave(0.0, 49.0) - 1.010) < 5e-4
+    assert abs(theory.langmuir_wave(0.0, 49.0) - 1.010) < 5e-4
+    wp = theory.cold_plasma_frequency(49.0)
+    assert abs(theory.langmuir_wave(1e-3, 49.0) / wp - 1 - 1.5e-6) < 1e-10
+    assert abs(theory.transverse_wave(1e4, 49.0) / 1e4 - 1) < 1e-8
