@@ -531,3 +531,52 @@ def test_thermalization_time_grows_as_rho_sp():
     t64 = _half_thermalization_time(4, precision=pic.PIC_FP64)[0]
     print("rho_sp = 4: t_th %.1f (mixed) %.1f (FP64)" % (res[4][0], t64))
     assert abs(t64 / res[4][0] - 1) <= 0.2
+
+
+# ---------------------------------------------------------------- thermal-mode branches (Sect. 3.1.1)
+
+def test_thermal_plasma_mode_branches_follow_the_dispersion_relations():
+    """Sect. 3.1.1: in an unmagnetized thermal electron-ion plasma (m_i/m_e = 49,
+    v_th = 0.1 c, Debye length = 1 cell, 10 cells per c/omega_pe) the Fourier modes
+    k_x of the fields oscillate on two branches that meet at k = 0: the Langmuir
+    wave (longitudinal e_x), omega^2 - omega_0^2 = 3 k^2 lambda_D^2 omega_pe^2,
+    and the transverse wave (e_y), omega^2 - omega_0^2 = k^2 c^2.  omega_0 is the
+    measured k = 0 oscillation (the relativistic shift of omega_P at this
+    temperature, 1.3 %, cancels).  A 256 x 8 box, 32 ppc per species, 100
+    plasma periods (bins of 0.01 omega_pe).  Bars: the Langmuir increments within
+    15 %, the transverse ones within 3 %."""
+    mu, theta, ppc, nx, ny, n_x, dt, every = 49.0, 0.01, 32, 256, 8, 10.0, 0.5, 2
+    n = ppc * nx * ny
+    d = pic.run_desc(2, nx, ny, 1, n_x, 2.0 * ppc, dt, [(-1.0, 1.0, n), (1.0, mu, n)])
+    nsamp = int(round(100 * 2 * np.pi * n_x / dt)) // every
+    ex = np.zeros((nsamp, nx // 2 + 1), complex)
+    ey = np.zeros((nsamp, nx // 2 + 1), complex)
+    with pic.Context([d], precision=pic.PIC_MIXED) as ctx:
+        ctx.load_maxwell_juttner(0, 0, ppc, theta, (0.0, 0.0, 0.0), seed=81)
+        ctx.load_maxwell_juttner(0, 1, ppc, theta / mu, (0.0, 0.0, 0.0), colocate_with=0, seed=82)
+        for q in range(nsamp):
+            ctx.step(every)
+            f = ctx.get_state(0, fields_only=True)[0]
+            ex[q] = np.fft.rfft(f[0, 0].mean(axis=0))
+            ey[q] = np.fft.rfft(f[1, 0].mean(axis=0))
+    win = np.hanning(nsamp)[:, None]
+    omega = 2 * np.pi * np.fft.fftfreq(nsamp, every * dt) * n_x          # units of omega_pe
+
+    def peak(series):
+        spec = np.abs(np.fft.fft((series - series.mean()) * win[:, 0])) ** 2
+        return abs(_peak(omega, spec, np.abs(omega) > 0.5))
+
+    w0 = peak(ex[:, 0])
+    kx = 2 * np.pi * np.arange(nx // 2 + 1) / nx                        # per cell
+    for m in (6, 8, 10):
+        k_lambda = kx[m] * (np.sqrt(theta) * n_x)                         # lambda_D = v_th / omega_pe in cells
+        inc = (peak(ex[:, m]) ** 2 - w0 ** 2) / (3 * k_lambda ** 2)
+        print("Langmuir m=%d k lambda_D=%.3f: increment ratio %.3f" % (m, k_lambda, inc))
+        assert abs(inc - 1) <= 0.15, (m, inc)
+    for m in (4, 8):
+        kc = kx[m] * n_x
+        inc = (peak(ey[:, m]) ** 2 - w0 ** 2) / kc ** 2
+        print("transverse m=%d kc/omega_pe=%.3f: increment ratio %.4f" % (m, kc, inc))
+        assert abs(inc - 1) <= 0.03, (m, inc)
+    print("omega_0 = %.4f omega_pe (cold omega_P %.4f)" % (w0, theory.cold_plasma_frequency(mu)))
+    assert abs(w0 / theory.cold_plasma_frequency(mu) - 1) <= 0.03
