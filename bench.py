@@ -445,7 +445,9 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                 "note": "set_state from pinned host + steps + get_state to pinned host"},
             "gpu_launches": int(m["counters"]["launches_per_step"] * m["steps"]),
             "clocks": m["clocks"],
-            "diag": {"gauss_max": m["diag"]["gauss_max"], "rho_max": m["diag"]["rho_max"]},
+            "diag": {"gauss_max": m["diag"]["gauss_max"], "rho_max": m["diag"]["rho_max"],
+                     "gauss_over_rho_max": m["diag"]["gauss_max"] / max(m["diag"]["rho_max"], 1e-300),
+                     "steps_since_load": int(m["diag"]["step"])},
         }
         if args.smooth > 0:
             # current smoothing: each pass reads and writes 3 x 8 B per interior cell (the in-place

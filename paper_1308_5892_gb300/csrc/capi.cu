@@ -201,6 +201,8 @@ FieldPtrs<R> fields_of(Run &r) {
     for (int c = 0; c < 3; ++c) {
         f.e[c] = F + (size_t)c * r.g.pcells;
         f.b[c] = F + (size_t)(3 + c) * r.g.pcells;
+        // the mixed path keeps the low-order part of e in planes 6..8 (see FieldPtrs)
+        f.el[c] = sizeof(R) == sizeof(float) ? F + (size_t)(6 + c) * r.g.pcells : nullptr;
     }
     return f;
 }
@@ -214,8 +216,9 @@ R *jplane(Run &r, int buf, int c) {
 
 // ------------------------------------------------------------ conversion kernels
 
+// dst_lo (nullable): receives the FP32 remainder v - (float)v (the low-order part of e in the mixed path).
 template <typename R>
-__global__ void k_pad_field(Geom g, const double *src, R *dst, int *err) {
+__global__ void k_pad_field(Geom g, const double *src, R *dst, R *dst_lo, int *err) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells;
          p += (long long)gridDim.x * blockDim.x) {
         const int pi = (int)(p % g.px);
@@ -225,6 +228,7 @@ __global__ void k_pad_field(Geom g, const double *src, R *dst, int *err) {
         const double v = src[((long long)k * g.ny + j) * g.nx + i];
         if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
         dst[p] = (R)v;
+        if (dst_lo) dst_lo[p] = (R)(v - (double)(R)v);
     }
 }
 
@@ -248,14 +252,16 @@ __global__ void k_check64(Geom g, Species64 s, long long n, int *err) {
     }
 }
 
+// src_lo (nullable): the low-order part added to src (e in the mixed path).
 template <typename R>
-__global__ void k_unpad_field(Geom g, const R *src, double *dst) {
+__global__ void k_unpad_field(Geom g, const R *src, const R *src_lo, double *dst) {
     const long long n = (long long)g.nx * g.ny * g.nz;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q % g.nx);
         const long long r = q / g.nx;
         const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-        dst[q] = (double)src[g.pidx(i, j, k)];
+        const long long p = g.pidx(i, j, k);
+        dst[q] = (double)src[p] + (src_lo ? (double)src_lo[p] : 0.0);
     }
 }
 
@@ -274,7 +280,8 @@ __global__ void k_upload_mixed(Geom g, const double *st, long long stride, long 
             }
             double f = floor(x);
             int ci = (int)f;
-            float off = (float)(x - f);
+            // the offset on the 2^-24 grid of the mixed path, where offset differences are exact (snap_offset)
+            float off = (float)(rint((x - f) * 16777216.0) * (1.0 / 16777216.0));
             if (off >= 1.0f) { off = 0.0f; ci += 1; }
             if (g.bcx == 1 && ax == 0 && ci >= g.nx) { ci = g.nx - 1; off = 1.0f; }
             else if (ci >= n3[ax]) ci -= n3[ax];
@@ -559,10 +566,11 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     r.inv_alpha_abs = d.n_x * d.n_x * d.rho_sp0 / 2.0;
     const size_t rs = real_size(ctx);
     const long long ncell = (long long)g.nx * g.ny * g.nz;
-    r.F = dev_alloc(ctx, 6 * rs * g.pcells);
+    const size_t fplanes = mixed ? 9 : 6;   // mixed: e, b and the low-order part of e
+    r.F = dev_alloc(ctx, fplanes * rs * g.pcells);
     r.J = dev_alloc(ctx, 6 * 8 * g.pcells);
     if (!r.F || !r.J) return fail(ctx, PIC_ENOMEM, "allocator returned NULL for the field arrays");
-    CK(cudaMemsetAsync(r.F, 0, 6 * rs * g.pcells, ctx->stream));
+    CK(cudaMemsetAsync(r.F, 0, fplanes * rs * g.pcells, ctx->stream));
     CK(cudaMemsetAsync(r.J, 0, 6 * 8 * g.pcells, ctx->stream));
     if (mixed) {
         r.nfA = (float4 *)dev_alloc(ctx, sizeof(float4) * g.pcells);
@@ -1284,9 +1292,11 @@ pic_status pic_set_state(pic_ctx *ctx, int run, const pic_state_view *in) {
         const double *src = fmap ? fmap + c * ncell : stg;
         if (!fmap) CK(cudaMemcpyAsync(stg, in->fields + c * ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, sm));
         if (ctx->precision == PIC_FP64)
-            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, src, (double *)r.F + c * g.pcells, ctx->d_err);
-        else
-            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(g, src, (float *)r.F + c * g.pcells, ctx->d_err);
+            k_pad_field<double><<<nblk(g.pcells), 256, 0, sm>>>(g, src, (double *)r.F + c * g.pcells, nullptr,
+                                                                ctx->d_err);
+        else   // e keeps its low-order part (plane 6 + c); b is FP32
+            k_pad_field<float><<<nblk(g.pcells), 256, 0, sm>>>(
+                g, src, (float *)r.F + c * g.pcells, c < 3 ? (float *)r.F + (6 + c) * g.pcells : nullptr, ctx->d_err);
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(r.J, 0, 6 * 8 * g.pcells, sm));
@@ -1369,9 +1379,10 @@ pic_status pic_get_state(pic_ctx *ctx, int run, pic_state_view *out) {
     for (int c = 0; c < 6; ++c) {
         double *dst = fmap ? fmap + c * ncell : stg;
         if (ctx->precision == PIC_FP64)
-            k_unpad_field<double><<<nblk(ncell), 256, 0, sm>>>(g, (double *)r.F + c * g.pcells, dst);
+            k_unpad_field<double><<<nblk(ncell), 256, 0, sm>>>(g, (double *)r.F + c * g.pcells, nullptr, dst);
         else
-            k_unpad_field<float><<<nblk(ncell), 256, 0, sm>>>(g, (float *)r.F + c * g.pcells, dst);
+            k_unpad_field<float><<<nblk(ncell), 256, 0, sm>>>(
+                g, (float *)r.F + c * g.pcells, c < 3 ? (float *)r.F + (6 + c) * g.pcells : nullptr, dst);
         if (!fmap)
             CK(cudaMemcpyAsync(out->fields + c * ncell, stg, sizeof(double) * ncell, cudaMemcpyDeviceToHost, sm));
     }

@@ -72,7 +72,7 @@ __global__ void k_field_diag(Geom g, FieldPtrs<R> f, double *acc, unsigned long 
         const long long p = interior_to_padded(g, q);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double e = (double)f.e[c][p], b = (double)f.b[c][p];
+            const double e = e_full(f, c, p), b = (double)f.b[c][p];
             if (!isfinite(e)) ++bad;
             if (!isfinite(b)) ++bad;
             v[c] += e * e;
@@ -170,9 +170,9 @@ __global__ void k_div_e(Geom g, FieldPtrs<R> f, double *out) {
         const int j = (int)(r % g.ny);
         const int k = (int)(r / g.ny);
         const long long c = g.pidx(i, j, k);
-        out[q] = ((double)f.e[0][c] - (double)f.e[0][g.widx(i - 1, j, k)]) +
-                 ((double)f.e[1][c] - (double)f.e[1][g.widx(i, j - 1, k)]) +
-                 ((double)f.e[2][c] - (double)f.e[2][g.widx(i, j, k - 1)]);
+        out[q] = (e_full(f, 0, c) - e_full(f, 0, g.widx(i - 1, j, k))) +
+                 (e_full(f, 1, c) - e_full(f, 1, g.widx(i, j - 1, k))) +
+                 (e_full(f, 2, c) - e_full(f, 2, g.widx(i, j, k - 1)));
     }
 }
 

@@ -12,6 +12,8 @@
 // Roofline: HBM bound.  Algorithmic bytes per cell: b advance 6 reads +
 // 3 writes; e advance 6 + 3 (J) reads, 3 writes, 3 zero-writes; node fields 6
 // reads + 8 writes, in units of sizeof(Real) (float4 pairs for node fields).
+#include <type_traits>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -145,7 +147,26 @@ __global__ void k_e_advance(Geom g, FieldPtrs<R> f, const R *J0, const R *J1, co
 }
 
 // Mixed path: the same update with the fixed-point current (int64, units of
-// 2^-36 of sgn(q) times the volume flux); scale = |alpha| 2^-36.
+// 2^-36 of sgn(q) times the volume flux); scale = |alpha| 2^-36.  e is the FP32
+// pair e + el (FieldPtrs), updated in FP64: the curl of the FP32 b values is
+// exact in FP64 (differences of FP32 numbers), the integer current converts
+// exactly, and the only rounding left is FP64's.  So div e - rho~ changes by
+// the rounding of the fluxes alone and does not drift with the FP32 rounding
+// of e (a single FP32 e made the Gauss residual grow by about 5e-9 of max rho
+// per step in a 128^3 thermal plasma).
+__device__ __forceinline__ double curl_exact(float a, float a_m, float b, float b_m) {
+    return ((double)a - (double)a_m) - ((double)b - (double)b_m);
+}
+
+// The pair's new value (e + el) + h curl + scale J, every operation rounded
+// separately (explicit intrinsics are never contracted into FMAs), so that the
+// single-run and the batched field kernels give bitwise the same fields.
+__device__ __forceinline__ double e_pair_update(const FieldPtrs<float> &f, int c, long long p, double h, double curl,
+                                                double scale, double j) {
+    const double e = __dadd_rn((double)f.e[c][p], (double)f.el[c][p]);
+    return __dadd_rn(__dadd_rn(e, __dmul_rn(h, curl)), __dmul_rn(scale, j));
+}
+
 __device__ __forceinline__ void e_fx_cell(const Geom &g, const FieldPtrs<float> &f, const unsigned long long *J0,
                                           const unsigned long long *J1, const unsigned long long *J2,
                                           unsigned long long *Z0, unsigned long long *Z1, unsigned long long *Z2,
@@ -156,19 +177,17 @@ __device__ __forceinline__ void e_fx_cell(const Geom &g, const FieldPtrs<float> 
         const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
         const long long c = g.pidx(i, j, k);
         const float bx = ld(f.b[0], c), by = ld(f.b[1], c), bz = ld(f.b[2], c);
-        const float curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
-        const float curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
-        const float curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
-        const float jx = (float)(scale * (double)(long long)folded_current(g, J0, i, j, k));
-        const float jy = (float)(scale * (double)(long long)folded_current(g, J1, i, j, k));
-        const float jz = (float)(scale * (double)(long long)folded_current(g, J2, i, j, k));
-        float ex = f.e[0][p] + dt * curl_x + jx;
-        float ey = f.e[1][p] + dt * curl_y + jy;
-        float ez = f.e[2][p] + dt * curl_z + jz;
-        if (g.bcx == 1 && i == 0) { ey = 0.f; ez = 0.f; }
-        f.e[0][p] = ex;
-        f.e[1][p] = ey;
-        f.e[2][p] = ez;
+        const double curl_x = curl_exact(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
+        const double curl_y = curl_exact(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
+        const double curl_z = curl_exact(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
+        const double h = (double)dt;
+        double ex = e_pair_update(f, 0, p, h, curl_x, scale, (double)(long long)folded_current(g, J0, i, j, k));
+        double ey = e_pair_update(f, 1, p, h, curl_y, scale, (double)(long long)folded_current(g, J1, i, j, k));
+        double ez = e_pair_update(f, 2, p, h, curl_z, scale, (double)(long long)folded_current(g, J2, i, j, k));
+        if (g.bcx == 1 && i == 0) { ey = 0.0; ez = 0.0; }
+        e_store(f, 0, p, ex);
+        e_store(f, 1, p, ey);
+        e_store(f, 2, p, ez);
         Z0[p] = 0ull;
         Z1[p] = 0ull;
         Z2[p] = 0ull;
@@ -199,19 +218,34 @@ __device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R
     const long long ncell = (long long)g.nx * g.ny * g.nz;
     const long long q = ((long long)k * g.ny + j) * g.nx + i;
     const R bx = ld(f.b[0], c), by = ld(f.b[1], c), bz = ld(f.b[2], c);
-    const R curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
-    const R curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
-    const R curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
-    const R jx = (R)(scale * (double)__ldg(Js + q));
-    const R jy = (R)(scale * (double)__ldg(Js + ncell + q));
-    const R jz = (R)(scale * (double)__ldg(Js + 2 * ncell + q));
-    R ex = f.e[0][p] + dt * curl_x + jx;
-    R ey = f.e[1][p] + dt * curl_y + jy;
-    R ez = f.e[2][p] + dt * curl_z + jz;
-    if (g.bcx == 1 && i == 0) { ey = R(0); ez = R(0); }
-    f.e[0][p] = ex;
-    f.e[1][p] = ey;
-    f.e[2][p] = ez;
+    if constexpr (std::is_same<R, float>::value) {
+        // the mixed path's FP32 pair, updated in FP64 as in e_fx_cell
+        const double curl_x = curl_exact(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
+        const double curl_y = curl_exact(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
+        const double curl_z = curl_exact(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
+        const double h = (double)dt;
+        double ex = e_pair_update(f, 0, p, h, curl_x, scale, (double)__ldg(Js + q));
+        double ey = e_pair_update(f, 1, p, h, curl_y, scale, (double)__ldg(Js + ncell + q));
+        double ez = e_pair_update(f, 2, p, h, curl_z, scale, (double)__ldg(Js + 2 * ncell + q));
+        if (g.bcx == 1 && i == 0) { ey = 0.0; ez = 0.0; }
+        e_store(f, 0, p, ex);
+        e_store(f, 1, p, ey);
+        e_store(f, 2, p, ez);
+    } else {
+        const R curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
+        const R curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
+        const R curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
+        const R jx = (R)(scale * (double)__ldg(Js + q));
+        const R jy = (R)(scale * (double)__ldg(Js + ncell + q));
+        const R jz = (R)(scale * (double)__ldg(Js + 2 * ncell + q));
+        R ex = f.e[0][p] + dt * curl_x + jx;
+        R ey = f.e[1][p] + dt * curl_y + jy;
+        R ez = f.e[2][p] + dt * curl_z + jz;
+        if (g.bcx == 1 && i == 0) { ey = R(0); ez = R(0); }
+        f.e[0][p] = ex;
+        f.e[1][p] = ey;
+        f.e[2][p] = ez;
+    }
     Z0[p] = ZT(0);
     Z1[p] = ZT(0);
     Z2[p] = ZT(0);
@@ -313,16 +347,21 @@ __global__ void __launch_bounds__(256) k_fields_multi(const FieldRunF *runs, con
 }
 
 template <typename R>
-__global__ void k_add_uniform(Geom g, FieldPtrs<R> f, R e0, R e1, R e2, R b0, R b1, R b2) {
+__global__ void k_add_uniform(Geom g, FieldPtrs<R> f, double e0, double e1, double e2, double b0, double b1,
+                              double b2) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.pcells; p += stride) {
         int pi, pj, pk;
         padded_coords(g, p, pi, pj, pk);
         const int i = g.wx(pi - g.G);
-        R v[6] = {e0, e1, e2, b0, b1, b2};
-        if (g.bcx == 1 && i == 0) { v[1] = R(0); v[2] = R(0); v[3] = R(0); }
-        f.e[0][p] += v[0]; f.e[1][p] += v[1]; f.e[2][p] += v[2];
-        f.b[0][p] += v[3]; f.b[1][p] += v[4]; f.b[2][p] += v[5];
+        double v[6] = {e0, e1, e2, b0, b1, b2};
+        if (g.bcx == 1 && i == 0) { v[1] = 0.0; v[2] = 0.0; v[3] = 0.0; }
+        if constexpr (std::is_same<R, float>::value) {
+            for (int c = 0; c < 3; ++c) e_store(f, c, p, __dadd_rn(e_full(f, c, p), v[c]));
+        } else {
+            f.e[0][p] += (R)v[0]; f.e[1][p] += (R)v[1]; f.e[2][p] += (R)v[2];
+        }
+        f.b[0][p] += (R)v[3]; f.b[1][p] += (R)v[4]; f.b[2][p] += (R)v[5];
     }
 }
 
@@ -373,8 +412,7 @@ void launch_e_advance_smoothed(const Geom &g, FieldPtrs<R> f, const CT *Js, doub
 
 template <typename R>
 void launch_add_uniform(const Geom &g, FieldPtrs<R> f, const double e0[3], const double b0[3], cudaStream_t s) {
-    k_add_uniform<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, (R)e0[0], (R)e0[1], (R)e0[2], (R)b0[0],
-                                                             (R)b0[1], (R)b0[2]);
+    k_add_uniform<R><<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, e0[0], e0[1], e0[2], b0[0], b0[1], b0[2]);
 }
 
 template void launch_b_advance<float>(const Geom &, FieldPtrs<float>, float, HistRef, cudaStream_t);

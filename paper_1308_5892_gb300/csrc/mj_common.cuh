@@ -213,7 +213,8 @@ __global__ void k_load_mj(LoadArgs a, Par par_of) {
                 for (int c = 0; c < a.ndim; ++c) {
                     const double f = floor(pos[c]);
                     int k = (int)f;
-                    float o = (float)(pos[c] - f);
+                    // the offset on the 2^-24 grid of the mixed path (see snap_offset)
+                    float o = (float)(rint((pos[c] - f) * 16777216.0) * (1.0 / 16777216.0));
                     if (o >= 1.0f) { o = 0.0f; k += 1; }
                     if (c == 0 && a.g.bcx == 1 && k >= n3[0]) { k = n3[0] - 1; o = 1.0f; }
                     else if (k >= n3[c]) k -= n3[c];

@@ -39,6 +39,18 @@ __device__ inline void boris(R u[3], const R E[3], const R B[3], R h, R dt) {
     u[2] = um[2] + (up[0] * s[1] - up[1] * s[0]) + qe * E[2];
 }
 
+// Offsets of the mixed path lie on the grid of 2^-24 cells: the difference of
+// two such values in [0, 1] is a multiple of 2^-24 below 1 in magnitude, hence
+// exact in FP32, so every piece displacement equals its end minus its start and
+// the pieces of a path telescope exactly to the stored move (the rounding of a
+// displacement would otherwise move the deposited charge away from the stored
+// position by up to half an ulp of the displacement, every step).  Identity in
+// FP64.
+template <typename R> __device__ inline R snap_offset(R x) { return x; }
+template <> __device__ inline float snap_offset<float>(float x) {
+    return rintf(x * 16777216.0f) * (1.0f / 16777216.0f);
+}
+
 // Current of one straight segment inside one cell: the particle (a cube of
 // volume 1) starts at offset d within the cell and moves by D.  With
 // mid-point weights W^0 = 1 - (d + D/2), W^1 = d + D/2, the flux through the x
@@ -163,7 +175,7 @@ struct PathSplit {
             R endp;
             if (rk(a) == k) endp = plo(a);
             else if (last) endp = d1[a];
-            else endp = cur[a] + dv[a] * (tn - tprev);
+            else endp = snap_offset<R>(cur[a] + dv[a] * (tn - tprev));
             D[a] = endp - cur[a];
             cur[a] = rk(a) == k ? pnew(a) : endp;
         }

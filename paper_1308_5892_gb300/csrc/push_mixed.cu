@@ -343,7 +343,7 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
     for (int ax = 0; ax < NDIM; ++ax) {
         const float pa = d[ax] + D[ax];
         float sa = floorf(pa);
-        float da = pa - sa;
+        float da = snap_offset<float>(pa - sa);   // the end offset on the 2^-24 grid
         if (da >= 1.f) { da = 0.f; sa += 1.f; }
         if (!(sa >= -1.f && sa <= 1.f)) {   // faster than one cell per step, or not finite:
             atomicOr(a.err, ERR_FAST_MOVE);  // flag it and keep every index in bounds
