@@ -105,11 +105,14 @@ typedef struct {
 /* Options of a context.
  *  precision      PIC_FP64: every quantity in double precision, plain
  *                 one-thread-per-particle kernel with global atomics.
- *                 PIC_MIXED: positions as cell index + FP32 offset, FP32
- *                 momenta and fields, currents summed exactly in fixed point
- *                 (each flux rounded once to 2^-26 of a particle's volume
- *                 flux, integer sums), particles kept sorted by tile; FP64
- *                 for diagnostics.
+ *                 PIC_MIXED: positions as cell index + FP32 offset (on a
+ *                 grid of 2^-24 cells), FP32 momenta and fields, currents
+ *                 summed exactly in fixed point (each flux rounded once to
+ *                 2^-26 of a particle's volume flux, integer sums), e carried
+ *                 as a pair of FP32 words (value and rounding remainder)
+ *                 updated in FP64 so that its rounding does not accumulate
+ *                 in div e, particles kept sorted by tile; FP64 for
+ *                 diagnostics.
  *  sort_interval  steps between re-sorts in PIC_MIXED (0: chosen by the autotuner)
  *  tile           tile shape in cells (0: chosen by the autotuner)
  *  stream         cudaStream_t to queue work on (NULL: default stream)
@@ -151,7 +154,10 @@ typedef struct {
  *  field_b[c]      |alpha|^-1 sum over cells of b_c^2 / 2 at t - dt/2
  *  sum_u[s][c]     sum over particles of u_c (= sum gamma v_c, the k = 0
  *                  momentum of Eq. Fourier)
- *  temperature[s]  <u . v> / 3 (equals Theta for a Maxwell-Juttner plasma)
+ *  temperature[s]  T_s / (m_e c^2) = (m_s/m_e) <u . v> / 3, the relativistic
+ *                  form of T = m <v^2> / 3 (Sect. 3.1.3); equals (m_s/m_e) Theta_s
+ *                  for a Maxwell-Juttner population of Theta_s = T / (m_s c^2),
+ *                  so species in thermal equilibrium report the same value
  *  gauss_max       max over nodes of |div e - S rho~|, rho~ = sum_s alpha_s W (CIC),
  *                  S the run's current smoothing (identity when off): smoothing the
  *                  current conserves div e - S rho~
@@ -342,7 +348,9 @@ pic_status pic_mj_sample_marginal(pic_ctx *ctx, double theta, double beta0, cons
  *  stream          cudaStream_t the work is queued on (NULL: default stream)
  * The call is asynchronous on `stream`.  The first call on a device looks up
  * the scratch array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call on a
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process: after cudaDeviceReset the array moves,
+ * so do not call this entry point after a reset.  Every call on a
  * device shares the one scratch array and clears it before use: calls whose
  * work overlaps on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  Returns PIC_EINVAL for invalid arguments and

@@ -70,6 +70,7 @@ def lib():
             "orc_run": ([G, P, P, P, ctypes.c_int, S, ctypes.c_int], None),
             "orc_stagger_back": ([G, P, P, ctypes.c_int, S], None),
             "orc_energies": ([G, P, P, ctypes.c_int, S, d, P], None),
+            "orc_temperature": ([ctypes.c_int, S, P], None),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -264,3 +265,13 @@ def energies(state: State):
     sp = state._species_array()
     lib().orc_energies(ctypes.byref(g), _ptr(state.e), _ptr(state.b), nsp, sp, state.inv_alpha_abs, _ptr(out))
     return {"kinetic": out[:nsp].copy(), "field_e": out[nsp:nsp + 3].copy(), "field_b": out[nsp + 3:].copy()}
+
+
+def temperature(state: State):
+    """Temperature per species in units of m_e c^2: (m_s/m_e) <u . v> / 3
+    (Sect. 3.1.3); equals (m_s/m_e) Theta for a Maxwell-Juttner population."""
+    nsp = len(state.species)
+    out = np.zeros(max(1, nsp))
+    sp = state._species_array()
+    lib().orc_temperature(nsp, sp, _ptr(out))
+    return out[:nsp].copy()

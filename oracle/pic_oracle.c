@@ -62,7 +62,7 @@ typedef struct {
     double alpha;      /* current coupling alpha_s = 2 sgn(q_s) / (n_x^2 rho_sp0), Eq. alpha */
 } orc_species;
 
-int orc_abi_version(void) { return 4; }
+int orc_abi_version(void) { return 5; }
 
 static long wrapi(long i, long n) { long r = i % n; return r < 0 ? r + n : r; }
 
@@ -579,5 +579,24 @@ void orc_energies(const orc_grid *g, const double *e, const double *b, int nsp, 
         }
         out[nsp + c] = 0.5 * ae * inv_alpha_abs;
         out[nsp + 3 + c] = 0.5 * ab * inv_alpha_abs;
+    }
+}
+
+/* Temperature of each species in units of m_e c^2 (Sect. 3.1.3 measures
+ * T = m <v^2> / 3; relativistically the mean is that of u . v, u = gamma v, so
+ * that a Maxwell-Juttner population of temperature Theta = T / (m_s c^2) gives
+ * exactly (m_s/m_e) Theta): out[s] = (m_s/m_e) (1/n) sum |u|^2 / gamma / 3,
+ * 0 for an empty species. */
+void orc_temperature(int nsp, const orc_species *sp, double *out) {
+    for (int s = 0; s < nsp; ++s) {
+        const orc_species *S = &sp[s];
+        double acc = 0.0;
+        for (int64_t p = 0; p < S->n; ++p) {
+            double ux = S->u[p], uy = S->u[S->n + p], uz = S->u[2 * S->n + p];
+            double u2 = ux * ux + uy * uy + uz * uz;
+            double gamma = sqrt(1.0 + u2);
+            acc += u2 / gamma;   /* u . v with v = u / gamma */
+        }
+        out[s] = S->n > 0 ? S->m_over_me * acc / (3.0 * (double)S->n) : 0.0;
     }
 }

@@ -9,6 +9,15 @@
   two-fluid limit, delta^2 = sum_s omega_ps^2 beta_s^2 / gamma_s over the beam
   populations, gives tau = (1/2 pi) sqrt(Gamma0) / beta0 T_pe for two electron
   beams of half density each on a positron background at rest.
+- Cold filamentation at a finite wavenumber (Sect. 3.2.1's cold setting):
+  for cold populations s streaming along z with beta_s, gamma_s and plasma
+  frequencies omega_ps, a perturbation E_z, B_y ~ exp(i k x + delta t) with k
+  across the flow obeys (cold relativistic two-fluid equations and Maxwell's
+  equations, lengths in c / omega_pe, rates in omega_pe)
+      delta^4 + (k^2 + A) delta^2 - k^2 C = 0,
+      A = sum_s omega_ps^2 / gamma_s^3,   C = sum_s omega_ps^2 beta_s^2 / gamma_s.
+  Its positive root grows with k towards sqrt(C), the k -> infinity rate that
+  the paper's tau formula states.
 - Unmagnetized thermal modes (Sect. 3.1.1): the transverse electromagnetic
   wave omega^2 = omega_P^2 + k^2 c^2 and the Langmuir wave
   omega^2 = omega_P^2 (1 + 3 k^2 lambda_D^2), lambda_D = v_th / omega_pe, with
@@ -40,6 +49,21 @@ def tau_filamentation_pair(beta0):
 def tau_filamentation_electron_beams(beta0):
     G0 = 1.0 / np.sqrt(1.0 - beta0 * beta0)
     return np.sqrt(G0) / beta0 / (2.0 * np.pi)
+
+
+def filamentation_rate_cold(kc, populations):
+    """delta / omega_pe of the purely growing filamentation mode at kc = k c /
+    omega_pe across the flow.  populations: iterable of (wp2, beta, gamma) with
+    wp2 = omega_ps^2 / omega_pe^2 (density and mass of population s relative to
+    the electrons that define omega_pe).  The positive root in delta^2 of
+    delta^4 + (k^2 + A) delta^2 - k^2 C = 0 (module docstring)."""
+    A = sum(w / g ** 3 for w, b, g in populations)
+    C = sum(w * b * b / g for w, b, g in populations)
+    k2 = kc * kc
+    p = k2 + A
+    # the positive root (sqrt(p^2 + 4 k^2 C) - p) / 2, written without cancellation
+    d2 = 2.0 * k2 * C / (np.sqrt(p * p + 4.0 * k2 * C) + p)
+    return np.sqrt(d2)
 
 
 def cold_plasma_frequency(mass_ratio):

@@ -1574,7 +1574,8 @@ pic_status pic_diagnostics(pic_ctx *ctx, int run, pic_diag *out) {
         out->count[s] = r.sp[s].n;
         out->kinetic[s] = r.sp[s].m_over_me * v[0];
         for (int c = 0; c < 3; ++c) out->sum_u[s][c] = v[1 + c];
-        out->temperature[s] = r.sp[s].n > 0 ? v[4] / (3.0 * (double)r.sp[s].n) : 0.0;
+        // T in units of m_e c^2: (m_s/m_e) <u . v> / 3 (Sect. 3.1.3)
+        out->temperature[s] = r.sp[s].n > 0 ? r.sp[s].m_over_me * v[4] / (3.0 * (double)r.sp[s].n) : 0.0;
         out->rho_max = std::max(out->rho_max, h[41 + s]);
     }
     out->gauss_max = h[48];

@@ -11,6 +11,7 @@
 // scratch is the file-scope device array below, which every GPU that loads
 // the library holds, whole, until the process exits.
 #include <cstdio>
+#include <mutex>
 
 #include "../../include/pic.h"
 #include "pic_internal.cuh"
@@ -24,8 +25,13 @@ constexpr long long kStaticCells = 1LL << 20;   // largest nx*ny*nz accepted (8 
 // Charge density of the nodes, shared by every call on this device.
 static __device__ __align__(256) double g_rho_static[kStaticCells];
 
-// Device address of g_rho_static per device, resolved once with that device current.
+// Device address of g_rho_static per device, resolved once with that device
+// current; the mutex makes the first resolution safe when several host threads
+// call at once.  The cache lives as long as the process: after cudaDeviceReset
+// the runtime reloads the module at another address, so the entry point must
+// not be used after a reset.
 double *g_rho_addr[64] = {nullptr};
+std::mutex g_rho_mutex;
 
 __global__ void k_zero_d(double *a, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -82,13 +88,17 @@ extern "C" pic_status pic_gauss_residual_static(int ndim, int nx, int ny, int nz
         if (counts[s] < 0 || (counts[s] > 0 && !pos[s])) return PIC_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PIC_ECUDA;
-    if (!g_rho_addr[dev]) {
-        // the symbol's device address, resolved on the current device (first call only)
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_rho_static) != cudaSuccess || !ptr) return PIC_ECUDA;
-        g_rho_addr[dev] = (double *)ptr;
+    double *rho = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_rho_mutex);
+        if (!g_rho_addr[dev]) {
+            // the symbol's device address, resolved on the current device (first call only)
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_rho_static) != cudaSuccess || !ptr) return PIC_ECUDA;
+            g_rho_addr[dev] = (double *)ptr;
+        }
+        rho = g_rho_addr[dev];
     }
-    double *rho = g_rho_addr[dev];
     cudaStream_t s = (cudaStream_t)stream;
     Geom g{};
     g.ndim = ndim; g.nx = nx; g.ny = ny; g.nz = nz;

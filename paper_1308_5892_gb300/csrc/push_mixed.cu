@@ -11,11 +11,20 @@
 //  - the current of the tile + halo is accumulated in shared memory in exact
 //    fixed point.  Every flux v (units of the particle volume times sgn q;
 //    |v| < 1 because |D| < dt < 1) is rounded once, x = rint(v 2^26), an
-//    int32, and x is added as two int32 limbs, hi += x >> 8 and lo += x & 255,
-//    so neither limb overflows however many particles a node collects.
+//    int32, and x is added as two int32 limbs, hi += x >> 12 and
+//    lo += x & 4095.  Range: the pieces of one particle move it by at most
+//    dt < 1 in all, so the fluxes one particle leaves at one slot sum to less
+//    than 1 in magnitude, and one slot receives at most 4 pieces of it.  A
+//    tile of N particles (all species) therefore puts |hi| < N 2^14 and
+//    lo < 4 N 2^12 into a slot: both stay below 2^31 while N < 2^17 = 131072.
+//    A tile works through its particles in rounds of at most 64 work items
+//    (65536 particles), and before a round that could bring the particles
+//    summed since the last flush to 2^17 the limbs are added to the global
+//    current and cleared, so no tile size or particle density can overflow
+//    them (dense filaments put several times the mean count into a tile).
 //    Integer sums are exact and associative, so the current does not depend
 //    on the order of the particles, on the tiling or on the sort interval.  At
-//    the end hi 2^18 + lo 2^10 (units 2^-36) is added once per node to the
+//    the end hi 2^22 + lo 2^10 (units 2^-36) is added once per node to the
 //    global int64 current.  The rounding, 2^-27 at most per flux, is below the
 //    FP32 rounding of the flux itself.  (FP32 shared atomics would serialise
 //    on the address conflicts that cell-sorted particles cause on every
@@ -187,7 +196,8 @@ __device__ __forceinline__ void acc_offset(int v, int &comp, int &di, int &dj, i
 
 // Start-cell fluxes of consecutive particles of one lane that start in the
 // same cell, summed exactly in registers (units 2^-26; at most 32 particles of
-// |v| < 1 each, so no overflow) and added to shared memory once per cell.
+// |v| <= |D| < dt < 2^-1/2 each, so |sum| < 2^30.5: no overflow) and added to
+// shared memory once per cell.
 template <int NDIM>
 struct RegAcc {
     static constexpr int NV = NDIM == 3 ? 12 : 8;
@@ -208,8 +218,8 @@ struct RegAcc {
             int comp, di, dj, dk;
             acc_offset<NDIM>(v, comp, di, dj, dk);
             const int q = comp * nodes + q0 + di + dj * sx + dk * sxy;
-            atomicAdd(Jhi + q, x[v] >> 8);
-            atomicAdd(Jlo + q, x[v] & 255);
+            atomicAdd(Jhi + q, x[v] >> 12);
+            atomicAdd(Jlo + q, x[v] & 4095);
         }
         q0 = -1;
     }
@@ -222,8 +232,8 @@ struct SmemSinkFx {
     __device__ __forceinline__ void operator()(int comp, int di, int dj, int dk, float v) {
         const int q = comp * nodes + base + di + dj * sx + dk * sxy;
         const int x = fx(v);
-        atomicAdd(hi + q, x >> 8);
-        atomicAdd(lo + q, x & 255);
+        atomicAdd(hi + q, x >> 12);
+        atomicAdd(lo + q, x & 4095);
     }
 };
 
@@ -276,6 +286,7 @@ __device__ __forceinline__ void tma_load(int ndim, uint32_t dst, const CUtensorM
 }
 
 constexpr int kQueue = 64;      // per-warp ring of waiting pieces (at most 63 wait at any time)
+constexpr int kRoundItems = 64; // work items per round of a tile (at most 64 x 1024 particles)
 constexpr int kStages = 3;      // per-warp particle prefetch ring
 // words of one particle in a stage: cell, NDIM offsets, 3 momenta
 template <int NDIM> __host__ __device__ constexpr int words_per_particle() { return NDIM + 4; }
@@ -463,6 +474,21 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
         mbar_wait_bounded(bar, 0, 1 << 22);
     }
 
+    // Add the tile's limbs to the padded global int64 current (CTA-wide; zero:
+    // clear them for a further round of deposits).
+    auto flush_limbs = [&](bool zero) {
+        for (int q = threadIdx.x; q < 3 * nodes; q += THREADS) {
+            const long long v = (long long)Jhi[q] * 4194304LL + (long long)Jlo[q] * 1024LL;   // 2^22, 2^10
+            if (zero) { Jhi[q] = 0; Jlo[q] = 0; }
+            if (v == 0) continue;
+            const int comp = q / nodes, r = q - comp * nodes;
+            const int lx = r % tc.Rx, ly = (r / tc.Rx) % tc.Ry, lz = r / tc.sxy;
+            const int gx = tc.x0 + lx, gy = tc.y0 + ly, gz = tc.z0 + lz;
+            if (gx < g.px && gy < g.py && gz < g.pz)
+                atomicAdd(a.J[comp] + ((long long)gz * g.py + gy) * g.px + gx, (unsigned long long)v);
+        }
+    };
+    long long since_flush = 0;   // particles summed into the limbs since they were last cleared (uniform)
     RegAcc<NDIM> acc;
     acc.q0 = -1;
     int qhead = 0, qcount = 0;   // warp-uniform state of the piece ring
@@ -488,12 +514,40 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
             }
             cp_async_commit();
         };
-        // work items are taken by whole warps from a shared counter
+        // queued pieces carry this species' sign: they are deposited before the
+        // species ends and before a flush of the limbs
+        auto drain_queue = [&]() {
+            if (qcount > 0) {
+                __syncwarp();
+                if (lane < qcount) drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, sgn);
+                __syncwarp();
+                qhead = (qhead + qcount) & (kQueue - 1);
+                qcount = 0;
+            }
+        };
+        for (int r0 = 0; r0 < nitems; r0 += kRoundItems) {
+        const int r1 = min(nitems, r0 + kRoundItems);
+        const bool need_flush = since_flush + (long long)(r1 - r0) * 1024 >= (1LL << 17);   // uniform
+        if (r0 > 0 || need_flush) {
+            // every warp has left the previous round; its pieces and register sums go to the limbs
+            drain_queue();
+            acc.flush(Jhi, Jlo, nodes, tc.sx, tc.sxy);
+            __syncthreads();
+            if (need_flush) {
+                flush_limbs(true);
+                since_flush = 0;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) work_ctr[sp] = r0;
+            __syncthreads();
+        }
+        since_flush += (long long)(r1 - r0) * 1024;
+        // work items of the round are taken by whole warps from a shared counter
         for (;;) {
             int item = 0;
             if (lane == 0) item = atomicAdd(&work_ctr[sp], 1);
             item = __shfl_sync(kFull, item, 0);
-            if (item >= nitems) break;
+            if (item >= r1) break;
             // block item: lane walks base + 32k + lane, k = 0..31 (consecutive ranks);
             // tail chunk: one element per lane in rank order
             const int base = item < nblk ? pbeg + (item << 10) : pbeg + (nblk << 10) + ((item - nblk) << 5);
@@ -596,28 +650,12 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                 kin_sh[1][warp] += a.m_over_me[sp] * (double)kin1;
             }
         }
-        // the queued pieces carry this species' sign: deposit them before the next species
-        if (qcount > 0) {
-            __syncwarp();
-            if (lane < qcount) drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, sgn);
-            __syncwarp();
-            qhead = (qhead + qcount) & (kQueue - 1);
-            qcount = 0;
-        }
+        }   // rounds
+        drain_queue();
     }
     acc.flush(Jhi, Jlo, nodes, tc.sx, tc.sxy);
     __syncthreads();
-
-    // Flush the tile current into the padded global int64 current.
-    for (int q = threadIdx.x; q < 3 * nodes; q += THREADS) {
-        const long long v = (long long)Jhi[q] * 262144LL + (long long)Jlo[q] * 1024LL;
-        if (v == 0) continue;
-        const int comp = q / nodes, r = q - comp * nodes;
-        const int lx = r % tc.Rx, ly = (r / tc.Rx) % tc.Ry, lz = r / tc.sxy;
-        const int gx = tc.x0 + lx, gy = tc.y0 + ly, gz = tc.z0 + lz;
-        if (gx < g.px && gy < g.py && gz < g.pz)
-            atomicAdd(a.J[comp] + ((long long)gz * g.py + gy) * g.px + gx, (unsigned long long)v);
-    }
+    flush_limbs(false);
     double *slot = a.hist.slot();
     if (slot && threadIdx.x < 2) {
         double t = 0.0;

@@ -70,7 +70,7 @@ def test_report_line_carries_the_contract_keys():
     args = types.SimpleNamespace(steps=20, warmup=3, no_cpu_baseline=True, smooth=1, gpus=1)
     w = dict(bench.WORKLOADS["thermal3d_128"], smooth=1)
     common = dict(ms_direct=160.0, field_ms=7.0, smooth_ms=1.3, ncell=128 ** 3, clocks={"sm_mhz": 2070.0},
-                  diag={"gauss_max": 1e-6, "rho_max": 1.5})
+                  diag={"gauss_max": 1e-6, "rho_max": 1.5, "step": 140})
     mixed = dict(common, ms=160.0, steps=20, push_ms=120.0, push_n=20, sort_ms=30.0,
                  counters={"bytes_per_particle_step": 56.0, "launches_per_step": 9.0},
                  tuning={"tile": [8, 8, 8], "sort_interval": 3, "halo": 3})

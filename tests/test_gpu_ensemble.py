@@ -3,11 +3,15 @@ launch per step) and the autotuner.  Both are checked for exactness: an
 ensemble member must be bitwise identical to the same run advanced alone, and
 a run advanced under the autotuner's trials must be bitwise identical to the
 same run advanced with the default tuning (each particle's arithmetic is the
-same and the current is an exact fixed-point sum)."""
+same and the current is an exact fixed-point sum).  Each member of an
+ensemble is also compared with the FP64 oracle stepped from its own uploaded
+(FP32-rounded) state, at the mixed path's parity bars."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1308_5892_gb300 as pic
+import synth
 
 pytestmark = pytest.mark.gpu
 
@@ -65,3 +69,79 @@ def test_autotuned_run_is_bitwise_equal_to_default_run():
     assert np.array_equal(fa, fb)
     for s in range(2):
         assert np.array_equal(pa[s], pb[s])
+
+
+# (nx, ny, particles per cell per species, field amplitude, smoothing passes)
+ORACLE_RUNS = [(32, 48, 4, 0.05, 0), (41, 37, 7, 0.02, 1), (64, 32, 3, 0.05, 0), (24, 56, 9, 0.03, 2),
+               (35, 33, 5, 0.05, 0)]
+WALL_RUNS = [(40, 32, 4, 0.03, 0), (29, 47, 6, 0.05, 0), (48, 24, 3, 0.02, 0)]
+
+
+def _rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / den if den > 0 else np.abs(a - b).max()
+
+
+def _member_vs_oracle(f, p, st, tol_field, tol_pos, tol_u, label):
+    ref = np.concatenate([st.e, st.b])
+    for c in range(6):
+        assert _rel(f[c], ref[c]) <= tol_field, (label, "field", c, _rel(f[c], ref[c]))
+    L = (st.nx, st.ny)
+    for s, sp in enumerate(st.species):
+        for a in range(2):
+            d = p[s][a] - sp.pos[a]
+            if not (a == 0 and st.bc_x == oracle.BC_CONDUCTOR):
+                d = d - L[a] * np.round(d / L[a])
+            assert np.abs(d).max() <= tol_pos, (label, "position", s, a, np.abs(d).max())
+        for a in range(3):
+            assert _rel(p[s][3 + a], sp.u[a]) <= tol_u, (label, "momentum", s, a)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_ensemble_members_match_oracle(walls):
+    """Uneven members (grids 24..64 cells per side, 3..9 particles per cell per
+    species, random fields and momenta, two members with current smoothing of
+    1 and 2 passes in the periodic ensemble; an ensemble between conducting
+    x-walls, App. A.4) advanced together by the batched kernels.  Every member
+    matches the oracle stepped from its own uploaded state: after 1 step at
+    the mixed bars (fields 1e-5 relative, positions 2e-6 cells, momenta 1e-5
+    relative), after 12 steps with re-sorts at 2e-4 (FP32 and FP64
+    trajectories separate by about 1e-7 per step)."""
+    runs = WALL_RUNS if walls else ORACLE_RUNS
+    bc = (1, 0, 0) if walls else (0, 0, 0)
+    descs, states = [], []
+    for r, (nx, ny, ppc, amp, sm) in enumerate(runs):
+        arr = synth.random_state_arrays(500 + r, 2, nx, ny, 1, ppc=ppc, spread=0.6, amp_e=amp, amp_b=amp,
+                                        colocate=False)
+        n = arr["species"][0]["pos"].shape[1]
+        descs.append(pic.run_desc(2, nx, ny, 1, 2.0, 8.0, 0.5, [(-1.0, 1.0, n), (1.0, 1.0, n)], bc=bc,
+                                  smooth_passes=sm))
+        states.append((np.concatenate([arr["e"], arr["b"]]), [np.concatenate([sp["pos"], sp["u"]])
+                                                              for sp in arr["species"]]))
+    with pic.Context(descs, precision=pic.PIC_MIXED, sort_interval=4) as ens:
+        for r, (fields, parts) in enumerate(states):
+            ens.set_state(r, fields, parts)
+        refs = []
+        for r, d in enumerate(descs):
+            f0, p0, _ = ens.get_state(r)
+            st = oracle.State.empty(2, d.nx, d.ny, 1, d.dt, d.n_x, d.rho_sp0, bc_x=d.bc[0],
+                                    smooth_passes=d.smooth_passes)
+            st.e[:] = f0[:3]
+            st.b[:] = f0[3:]
+            for s, q in zip(range(2), (-1.0, 1.0)):
+                st.species.append(oracle.Species(np.ascontiguousarray(p0[s][:3]), np.ascontiguousarray(p0[s][3:]),
+                                                 q, 1.0))
+            refs.append(st)
+        ens.step(1)
+        for r, st in enumerate(refs):
+            oracle.step(st)
+            f, p, step = ens.get_state(r)
+            assert step == 1
+            _member_vs_oracle(f, p, st, 1e-5, 2e-6, 1e-5, (walls, r, 1))
+        ens.step(11)
+        for r, st in enumerate(refs):
+            oracle.step(st, 11)
+            f, p, step = ens.get_state(r)
+            assert step == 12
+            _member_vs_oracle(f, p, st, 2e-4, 2e-4, 2e-4, (walls, r, 12))
+

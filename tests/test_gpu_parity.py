@@ -104,6 +104,37 @@ def test_fp64_diagnostics_match_oracle():
         assert np.allclose(d["sum_u"][s], st.species[s].u.sum(1), rtol=1e-12, atol=1e-9)
 
 
+ION_ELECTRON = (synth.SpeciesSpec(-1.0, 1.0), synth.SpeciesSpec(+1.0, 25.0))
+
+
+@pytest.mark.parametrize("precision,tol", [(pic.PIC_FP64, 1e-12), (pic.PIC_MIXED, 1e-6)])
+def test_diagnostics_with_a_heavy_species_match_oracle(precision, tol):
+    """Temperature (m_s/m_e) <u . v>/3 and kinetic energy sum (m_s/m_e)(gamma - 1)
+    of an electron-ion state (m_i/m_e = 25, Sect. 3.1.3, App. A.2) against the
+    oracle's pinned functions, on the uploaded state and after 3 steps: FP64
+    to 1e-12, mixed to 1e-6 (its FP32 momenta differ from the oracle's FP64
+    trajectories at about 1e-7 per step)."""
+    desc, fields, parts, arr = _make(3, (12, 10, 8), 6, seed=17, spread=0.8, amp=0.05, colocate=False,
+                                     species=ION_ELECTRON)
+    with pic.Context([desc], precision=precision) as ctx:
+        ctx.set_state(0, fields, parts)
+        f0, p0, _ = ctx.get_state(0)
+        d0 = ctx.diagnostics(0)
+        ctx.step(3)
+        d3 = ctx.diagnostics(0)
+    st = _oracle_state(desc, f0, p0, arr)
+    for d, label in ((d0, "uploaded"), (None, "after 3 steps")):
+        if d is None:
+            oracle.step(st, 3)
+            d = d3
+        T = oracle.temperature(st)
+        en = oracle.energies(st)
+        assert np.allclose(d["temperature"], T, rtol=tol), (label, d["temperature"], T)
+        assert np.allclose(d["kinetic"], en["kinetic"], rtol=tol), (label, d["kinetic"], en["kinetic"])
+    # the heavy species' temperature carries its mass: u.v/3 alone would be 25x smaller
+    assert d0["temperature"][1] > 5 * d0["temperature"][0]
+
+
 def test_fp64_neutral_start_keeps_gauss_to_roundoff():
     desc, fields, parts, arr = _make(3, (10, 12, 8), 4, seed=9, spread=1.5, amp=0.0, colocate=True)
     fields[3:] = np.random.default_rng(1).normal(0, 0.05, fields[3:].shape)
@@ -281,16 +312,18 @@ def test_mixed_empty_species_and_boundary_positions():
 
 
 def test_mixed_energy_history_tracks_oracle():
-    desc, fields, parts, arr = _make(2, (32, 32, 1), 8, seed=11, spread=0.5, amp=0.0, colocate=True)
+    desc, fields, parts, arr = _make(2, (32, 32, 1), 8, seed=11, spread=0.5, amp=0.0, colocate=True,
+                                     species=ION_ELECTRON)
     ctx, st = _mixed_roundtrip(desc, fields, parts, arr)
     with ctx:
         ctx.step(10)
         hist = ctx.energy_history(0)
     assert hist.shape == (10, 4)
-    # step 0 kinetic at t_0 is the average of gamma-1 over u^{-1/2} and u^{1/2}
-    ek_minus = sum(sp.m_over_me * (np.sqrt(1 + (sp.u ** 2).sum(0)) - 1).sum() for sp in st.species)
+    # step 0 kinetic at t_0 is the average of the oracle's kinetic energy (pinned,
+    # with the species masses) over u^{-1/2} and u^{1/2}
+    ek_minus = oracle.energies(st)["kinetic"].sum()
     oracle.step(st)
-    ek_plus = sum(sp.m_over_me * (np.sqrt(1 + (sp.u ** 2).sum(0)) - 1).sum() for sp in st.species)
+    ek_plus = oracle.energies(st)["kinetic"].sum()
     assert np.isclose(hist[0, 0], 0.5 * (ek_minus + ek_plus), rtol=1e-5)
     assert np.all(np.isfinite(hist))
 

@@ -399,6 +399,54 @@ def test_field_energy_units():
     assert np.isclose(en["field_e"][0], 16 * 0.5 * 4.0 / (2.0 / (9.0 * 10.0)))
 
 
+def _two_species_exact_gammas():
+    """A heavy species (m/m_e = 25) and an electron species whose momenta have
+    exact Lorentz factors: |u|^2 = 3, 8, 0.5625 give gamma = 2, 3, 1.25, and
+    |u|^2 = 24, 0.5625 give gamma = 5, 1.25."""
+    st = _state(3, (4, 4, 4))
+    u_ion = np.array([[0.0, 2.0, 0.75], [0.0, 2.0, 0.0], [np.sqrt(3.0), 0.0, 0.0]])
+    u_el = np.array([[2.0, -0.75], [2.0, 0.0], [4.0, 0.0]])
+    st.species.append(oracle.Species(np.zeros((3, 3)), np.ascontiguousarray(u_ion), 1.0, 25.0))
+    st.species.append(oracle.Species(np.zeros((3, 2)), np.ascontiguousarray(u_el), -1.0, 1.0))
+    return st
+
+
+def test_kinetic_energy_counts_the_species_mass():
+    """App. A.2 energy units: the kinetic energy is sum (m_s/m_e)(gamma - 1).
+    Worked by hand: ions 25 (1 + 2 + 0.25) = 81.25, electrons 4 + 0.25 = 4.25.
+    Dropping the mass factor would give 3.25 for the ions."""
+    en = oracle.energies(_two_species_exact_gammas())
+    assert abs(en["kinetic"][0] - 81.25) < 1e-12
+    assert abs(en["kinetic"][1] - 4.25) < 1e-12
+
+
+def test_temperature_is_mass_times_mean_u_dot_v_over_3():
+    """Sect. 3.1.3: T = m <v^2>/3, relativistically (m_s/m_e) <u . v>/3 in
+    units of m_e c^2 (u . v = |u|^2/gamma).  Worked by hand: ions 25 (3/2 +
+    8/3 + 0.45)/9 = 1385/108, electrons (24/5 + 0.45)/6 = 7/8."""
+    T = oracle.temperature(_two_species_exact_gammas())
+    assert abs(T[0] - 1385.0 / 108.0) < 1e-12
+    assert abs(T[1] - 0.875) < 1e-14
+
+
+def test_temperature_of_maxwell_juttner_ions_is_mass_times_theta():
+    """A Maxwell-Juttner population of Theta = T/(m c^2) has <u . v> = 3 Theta
+    (Table averages of Sect. 4), so ions of m_i/m_e = 25 loaded at Theta =
+    0.04 report T = 1 m_e c^2, and electrons at Theta = 1 report 1: the two
+    species of a plasma in equilibrium share T (within 4 sigma of the sample)."""
+    from oracle import mj
+    n = 100000
+    st = _state(3, (8, 8, 8))
+    for seed, theta, m in ((21, 0.04, 25.0), (22, 1.0, 1.0)):
+        w = mj.uniforms(seed, 0, np.arange(n))
+        u = mj.sample_momenta(w[3], w[4], w[5], theta, np.zeros(3))
+        st.species.append(oracle.Species(np.zeros((3, n)), np.ascontiguousarray(u), 1.0, m))
+        uv = (u ** 2).sum(0) / np.sqrt(1 + (u ** 2).sum(0))
+        sigma = m * uv.std() / 3 / np.sqrt(n)
+        T = oracle.temperature(st)[-1]
+        assert abs(T - 1.0) < 4 * sigma, (theta, m, T, sigma)
+
+
 def test_thermal_plasma_k0_oscillation_is_at_the_relativistic_cutoff():
     """Sect. 3.1: the k = 0 electric field of a thermal pair plasma oscillates
     at omega_cut = omega_P <gamma^-1 (1 - beta^2/3)>^(1/2), omega_P^2 = 2/n_x^2
