@@ -142,9 +142,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _time_oracle_sample(w, steps, seed):
+def _time_oracle_sample(w, steps, seed, parallel=False):
     """FP64 oracle on a 32^3 (3D) or 64^2 (2D) box with the workload's ppc and
-    temperature; returns (particle-steps/ns, seconds, particles, steps, sizes)."""
+    temperature, serial (the parity reference build) or with the particle loop
+    on all host cores (its OpenMP build); returns (particle-steps/ns, seconds,
+    particles, steps, sizes, threads)."""
     import oracle
     sw = dict(w)
     if w.get("ensemble"):   # one representative member of the ensemble
@@ -155,10 +157,20 @@ def _time_oracle_sample(w, steps, seed):
     else:
         sw.update(nx=min(w["nx"], 64), ny=min(w["ny"], 64), nz=1)
     st, npart = _oracle_state(w, seed, sw["nx"], sw["ny"], sw["nz"])
+    threads = oracle.lib_parallel().orc_threads(os.cpu_count() or 1) if parallel else 1
     t0 = time.perf_counter()
-    oracle.step(st, steps)
+    if parallel:
+        oracle.step_parallel(st, steps, threads)
+    else:
+        oracle.step(st, steps)
     dt = time.perf_counter() - t0
-    return npart * steps / (dt * 1e9), dt, npart, steps, sw
+    return npart * steps / (dt * 1e9), dt, npart, steps, sw, threads
+
+
+def _oracle_sample_text(w, sw, npart, threads):
+    return ("FP64 oracle, 1 step per timed step on a %dx%dx%d box, %d ppc/species, theta=%g (%d particles), "
+            "particle loop on %d host thread%s" % (sw["nx"], sw["ny"], sw["nz"] if w["ndim"] == 3 else 1, w["ppc"],
+                                                   w["theta"], npart, threads, "" if threads == 1 else "s"))
 
 
 def rank_env():
@@ -194,20 +206,22 @@ def run_reference(args, w):
         return 0
     times = []
     for k in range(args.warmup + args.steps):
-        v, dt, npart, nst, sw = _time_oracle_sample(w, 1, seed=1000 + k)
+        v, dt, npart, nst, sw, threads = _time_oracle_sample(w, 1, seed=1000 + k, parallel=True)
         if k >= args.warmup:
             times.append(dt)
     npart_steps = npart * args.steps
     total = sum(times)
     val = npart_steps / (total * 1e9)
-    sample = "FP64 oracle, 1 step per timed step on a %dx%dx%d box, %d ppc/species, theta=%g (%d particles)" % (
-        sw["nx"], sw["ny"], sw["nz"] if w["ndim"] == 3 else 1, w["ppc"], w["theta"], npart)
+    sample = _oracle_sample_text(w, sw, npart, threads)
+    v1, dt1, _, _, _, _ = _time_oracle_sample(w, 1, seed=999)   # the plain build on one core, for context
     out = {"impl": "reference", "metric": "particle-steps/ns", "value": val, "unit": "particle-steps/ns",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w["name"], "sample": sample},
-           "cpu_baseline": {"value": val, "unit": "particle-steps/ns", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": val, "unit": "particle-steps/ns", "cores": threads, "kind": "oracle",
+                            "sample": sample, "host_cores": os.cpu_count(),
+                            "single_core": {"value": v1, "cores": 1, "seconds_per_step": dt1}},
            "e2e": {"value": val, "unit": "particle-steps/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
@@ -462,10 +476,12 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                 "algorithmic_bytes_per_step": bytes_step, "achieved": ach, "unit": "GB/s",
                 "frac": None if ach is None else ach / peak}
         if not args.no_cpu_baseline:
-            v, dt, npp, nst, sw = _time_oracle_sample(w, 1, seed=77)
-            out["cpu_baseline"] = {"value": v, "unit": "particle-steps/ns", "cores": 1, "kind": "oracle",
-                                   "sample": "1 step of the FP64 oracle on a %dx%dx%d box with the same ppc and theta "
-                                             "(%d particles, %.1f s)" % (sw["nx"], sw["ny"], sw["nz"] if w["ndim"] == 3 else 1, npp, dt)}
+            v, dt, npp, nst, sw, threads = _time_oracle_sample(w, 1, seed=77, parallel=True)
+            v1, dt1, _, _, _, _ = _time_oracle_sample(w, 1, seed=78)
+            out["cpu_baseline"] = {"value": v, "unit": "particle-steps/ns", "cores": threads, "kind": "oracle",
+                                   "sample": _oracle_sample_text(w, sw, npp, threads) + " (%.2f s)" % dt,
+                                   "host_cores": os.cpu_count(),
+                                   "single_core": {"value": v1, "cores": 1, "seconds_per_step": dt1}}
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()

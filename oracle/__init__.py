@@ -30,6 +30,7 @@ BC_PERIODIC = 0
 BC_CONDUCTOR = 1
 
 _lib = None
+_lib_omp = None
 
 
 class _Grid(ctypes.Structure):
@@ -48,36 +49,52 @@ def lib():
     """Load (building if needed) the C oracle."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        P = ctypes.c_void_p
-        G = ctypes.POINTER(_Grid)
-        S = ctypes.POINTER(_Species)
-        i64 = ctypes.c_int64
-        d = ctypes.c_double
-        sigs = {
-            "orc_abi_version": ([], ctypes.c_int),
-            "orc_b_advance": ([G, P, P, d], None),
-            "orc_e_advance": ([G, P, P, d], None),
-            "orc_node_fields": ([G, P, P, P], None),
-            "orc_gather": ([G, P, P, i64, P, P], None),
-            "orc_boris": ([i64, P, P, d, d], None),
-            "orc_deposit": ([G, P, i64, P, P, d], None),
-            "orc_rho": ([G, i64, P, d, P], None),
-            "orc_div_e": ([G, P, P], None),
-            "orc_smooth": ([G, P, ctypes.c_int, ctypes.c_int], None),
-            "orc_step": ([G, P, P, P, ctypes.c_int, S], None),
-            "orc_run": ([G, P, P, P, ctypes.c_int, S, ctypes.c_int], None),
-            "orc_stagger_back": ([G, P, P, ctypes.c_int, S], None),
-            "orc_energies": ([G, P, P, ctypes.c_int, S, d, P], None),
-            "orc_temperature": ([ctypes.c_int, S, P], None),
-        }
-        for name, (args, res) in sigs.items():
-            fn = getattr(L, name)
-            fn.argtypes = args
-            fn.restype = res
-        _lib = L
+        _lib = _load(_build.build())
     return _lib
+
+
+def lib_parallel():
+    """The OpenMP build of the same source: the particle loop is shared between
+    threads, each depositing into its own current grid (only the order of the
+    FP64 current sums differs).  Used for the all-cores timing of the CPU
+    baseline; the plain build above is the parity reference."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _load(_build.build(openmp=True))
+    return _lib_omp
+
+
+def _load(path):
+    """Load one build of the C oracle and declare its entry points."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    G = ctypes.POINTER(_Grid)
+    S = ctypes.POINTER(_Species)
+    i64 = ctypes.c_int64
+    d = ctypes.c_double
+    sigs = {
+        "orc_abi_version": ([], ctypes.c_int),
+        "orc_b_advance": ([G, P, P, d], None),
+        "orc_e_advance": ([G, P, P, d], None),
+        "orc_node_fields": ([G, P, P, P], None),
+        "orc_gather": ([G, P, P, i64, P, P], None),
+        "orc_boris": ([i64, P, P, d, d], None),
+        "orc_deposit": ([G, P, i64, P, P, d], None),
+        "orc_rho": ([G, i64, P, d, P], None),
+        "orc_div_e": ([G, P, P], None),
+        "orc_smooth": ([G, P, ctypes.c_int, ctypes.c_int], None),
+        "orc_step": ([G, P, P, P, ctypes.c_int, S], None),
+        "orc_run": ([G, P, P, P, ctypes.c_int, S, ctypes.c_int], None),
+        "orc_stagger_back": ([G, P, P, ctypes.c_int, S], None),
+        "orc_energies": ([G, P, P, ctypes.c_int, S, d, P], None),
+        "orc_temperature": ([ctypes.c_int, S, P], None),
+        "orc_threads": ([ctypes.c_int], ctypes.c_int),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
 
 
 def _ptr(a):
@@ -164,6 +181,18 @@ def step(state: State, nsteps: int = 1, J=None):
     sp = state._species_array()
     lib().orc_run(ctypes.byref(g), _ptr(state.e), _ptr(state.b), _ptr(J), len(state.species), sp, nsteps)
     return J
+
+
+def step_parallel(state: State, nsteps: int = 1, threads: int = 0):
+    """step() with the OpenMP build on `threads` threads (0: all the host's
+    cores); returns the number of threads used."""
+    L = lib_parallel()
+    used = L.orc_threads(threads)
+    g = state.grid()
+    J = np.zeros_like(state.e)
+    sp = state._species_array()
+    L.orc_run(ctypes.byref(g), _ptr(state.e), _ptr(state.b), _ptr(J), len(state.species), sp, nsteps)
+    return used
 
 
 def stagger_back(state: State):

@@ -147,47 +147,80 @@ __global__ void k_e_advance(Geom g, FieldPtrs<R> f, const R *J0, const R *J1, co
 }
 
 // Mixed path: the same update with the fixed-point current (int64, units of
-// 2^-36 of sgn(q) times the volume flux); scale = |alpha| 2^-36.  e is the FP32
-// pair e + el (FieldPtrs), updated in FP64: the curl of the FP32 b values is
-// exact in FP64 (differences of FP32 numbers), the integer current converts
-// exactly, and the only rounding left is FP64's.  So div e - rho~ changes by
-// the rounding of the fluxes alone and does not drift with the FP32 rounding
-// of e (a single FP32 e made the Gauss residual grow by about 5e-9 of max rho
-// per step in a 128^3 thermal plasma).
-__device__ __forceinline__ double curl_exact(float a, float a_m, float b, float b_m) {
-    return ((double)a - (double)a_m) - ((double)b - (double)b_m);
+// 2^-36 of sgn(q) times the volume flux); scale = |alpha| 2^-36, passed as an
+// FP32 pair (scale_hi + scale_lo).  e is the FP32 pair e + el (FieldPtrs),
+// updated with error-free FP32 transformations (Knuth's TwoSum, and the
+// FMA-based exact product): the curl of the FP32 b values, the converted
+// integer current and the sum are all carried to about 2^-48 relative, so
+// div e - rho~ changes by the rounding of the fluxes alone and does not drift
+// with the FP32 rounding of e (a single FP32 e made the Gauss residual grow by
+// about 5e-9 of max rho per step in a 128^3 thermal plasma).  The FP32 pipe
+// does this at a small fraction of the cost of the same update in FP64.
+// Every operation is an explicit round-to-nearest intrinsic, never contracted,
+// so the single-run and the batched field kernels give bitwise the same fields.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, err};
 }
-
-// The pair's new value (e + el) + h curl + scale J, every operation rounded
-// separately (explicit intrinsics are never contracted into FMAs), so that the
-// single-run and the batched field kernels give bitwise the same fields.
-__device__ __forceinline__ double e_pair_update(const FieldPtrs<float> &f, int c, long long p, double h, double curl,
-                                                double scale, double j) {
-    const double e = __dadd_rn((double)f.e[c][p], (double)f.el[c][p]);
-    return __dadd_rn(__dadd_rn(e, __dmul_rn(h, curl)), __dmul_rn(scale, j));
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// curl component (a - a_m) - (b - b_m) of four FP32 values, as a pair
+__device__ __forceinline__ F2 curl_pair(float a, float a_m, float b, float b_m) {
+    const F2 d1 = two_sum(a, -a_m), d2 = two_sum(b, -b_m);
+    const F2 c = two_sum(d1.hi, -d2.hi);
+    return {c.hi, __fadd_rn(__fsub_rn(d1.lo, d2.lo), c.lo)};
+}
+// an int64 as a pair of FP32 values whose sum is exact (|J| < 2^48)
+__device__ __forceinline__ F2 ll_pair(long long J) {
+    const float h = __ll2float_rn(J);
+    return {h, __ll2float_rn(J - (long long)h)};
+}
+// The pair's new value (e + el) + h curl + scale J, renormalised.
+__device__ __forceinline__ F2 e_pair_update(const FieldPtrs<float> &f, int c, long long p, float h, F2 curl,
+                                            F2 scale, long long J) {
+    const F2 hc = two_prod(h, curl.hi);
+    const F2 j = ll_pair(J);
+    const F2 sj = two_prod(scale.hi, j.hi);
+    const float hc_lo = __fmaf_rn(h, curl.lo, hc.lo);
+    const float sj_lo = __fadd_rn(sj.lo, __fadd_rn(__fmul_rn(scale.hi, j.lo), __fmul_rn(scale.lo, j.hi)));
+    const F2 s1 = two_sum(f.e[c][p], hc.hi);
+    const F2 s2 = two_sum(s1.hi, sj.hi);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(f.el[c][p], hc_lo), __fadd_rn(sj_lo, s1.lo)), s2.lo);
+    const float hi = __fadd_rn(s2.hi, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s2.hi))};
+}
+__device__ __forceinline__ void e_pair_store(const FieldPtrs<float> &f, int c, long long p, F2 v) {
+    f.e[c][p] = v.hi;
+    f.el[c][p] = v.lo;
 }
 
 __device__ __forceinline__ void e_fx_cell(const Geom &g, const FieldPtrs<float> &f, const unsigned long long *J0,
                                           const unsigned long long *J1, const unsigned long long *J2,
                                           unsigned long long *Z0, unsigned long long *Z1, unsigned long long *Z2,
-                                          float dt, double scale, long long p) {
+                                          float dt, F2 scale, long long p) {
     {
         int pi, pj, pk;
         padded_coords(g, p, pi, pj, pk);
         const int i = g.wx(pi - g.G), j = g.wy(pj - g.G), k = g.wz(pk - g.Gz);
         const long long c = g.pidx(i, j, k);
         const float bx = ld(f.b[0], c), by = ld(f.b[1], c), bz = ld(f.b[2], c);
-        const double curl_x = curl_exact(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
-        const double curl_y = curl_exact(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
-        const double curl_z = curl_exact(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
-        const double h = (double)dt;
-        double ex = e_pair_update(f, 0, p, h, curl_x, scale, (double)(long long)folded_current(g, J0, i, j, k));
-        double ey = e_pair_update(f, 1, p, h, curl_y, scale, (double)(long long)folded_current(g, J1, i, j, k));
-        double ez = e_pair_update(f, 2, p, h, curl_z, scale, (double)(long long)folded_current(g, J2, i, j, k));
-        if (g.bcx == 1 && i == 0) { ey = 0.0; ez = 0.0; }
-        e_store(f, 0, p, ex);
-        e_store(f, 1, p, ey);
-        e_store(f, 2, p, ez);
+        const F2 curl_x = curl_pair(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
+        const F2 curl_y = curl_pair(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
+        const F2 curl_z = curl_pair(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
+        F2 ex = e_pair_update(f, 0, p, dt, curl_x, scale, (long long)folded_current(g, J0, i, j, k));
+        F2 ey = e_pair_update(f, 1, p, dt, curl_y, scale, (long long)folded_current(g, J1, i, j, k));
+        F2 ez = e_pair_update(f, 2, p, dt, curl_z, scale, (long long)folded_current(g, J2, i, j, k));
+        if (g.bcx == 1 && i == 0) { ey = F2{0.f, 0.f}; ez = F2{0.f, 0.f}; }
+        e_pair_store(f, 0, p, ex);
+        e_pair_store(f, 1, p, ey);
+        e_pair_store(f, 2, p, ez);
         Z0[p] = 0ull;
         Z1[p] = 0ull;
         Z2[p] = 0ull;
@@ -196,7 +229,7 @@ __device__ __forceinline__ void e_fx_cell(const Geom &g, const FieldPtrs<float> 
 
 __global__ void k_e_advance_fx(Geom g, FieldPtrs<float> f, const unsigned long long *J0,
                                const unsigned long long *J1, const unsigned long long *J2, unsigned long long *Z0,
-                               unsigned long long *Z1, unsigned long long *Z2, float dt, double scale,
+                               unsigned long long *Z1, unsigned long long *Z2, float dt, F2 scale,
                                long long *hist_inc) {
     // no kernel of this launch reads the counter; the next step's kernels see the new value
     if (hist_inc && blockIdx.x == 0 && threadIdx.x == 0) *hist_inc += 1;
@@ -219,18 +252,18 @@ __device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R
     const long long q = ((long long)k * g.ny + j) * g.nx + i;
     const R bx = ld(f.b[0], c), by = ld(f.b[1], c), bz = ld(f.b[2], c);
     if constexpr (std::is_same<R, float>::value) {
-        // the mixed path's FP32 pair, updated in FP64 as in e_fx_cell
-        const double curl_x = curl_exact(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
-        const double curl_y = curl_exact(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
-        const double curl_z = curl_exact(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
-        const double h = (double)dt;
-        double ex = e_pair_update(f, 0, p, h, curl_x, scale, (double)__ldg(Js + q));
-        double ey = e_pair_update(f, 1, p, h, curl_y, scale, (double)__ldg(Js + ncell + q));
-        double ez = e_pair_update(f, 2, p, h, curl_z, scale, (double)__ldg(Js + 2 * ncell + q));
-        if (g.bcx == 1 && i == 0) { ey = 0.0; ez = 0.0; }
-        e_store(f, 0, p, ex);
-        e_store(f, 1, p, ey);
-        e_store(f, 2, p, ez);
+        // the mixed path's FP32 pair, updated as in e_fx_cell (the smoothed current is int64 fixed point)
+        const F2 sc = {(float)scale, (float)(scale - (double)(float)scale)};
+        const F2 curl_x = curl_pair(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
+        const F2 curl_y = curl_pair(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
+        const F2 curl_z = curl_pair(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
+        F2 ex = e_pair_update(f, 0, p, dt, curl_x, sc, (long long)__ldg(Js + q));
+        F2 ey = e_pair_update(f, 1, p, dt, curl_y, sc, (long long)__ldg(Js + ncell + q));
+        F2 ez = e_pair_update(f, 2, p, dt, curl_z, sc, (long long)__ldg(Js + 2 * ncell + q));
+        if (g.bcx == 1 && i == 0) { ey = F2{0.f, 0.f}; ez = F2{0.f, 0.f}; }
+        e_pair_store(f, 0, p, ex);
+        e_pair_store(f, 1, p, ey);
+        e_pair_store(f, 2, p, ez);
     } else {
         const R curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
         const R curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
@@ -341,7 +374,8 @@ __global__ void __launch_bounds__(256) k_fields_multi(const FieldRunF *runs, con
                 e_smoothed_cell<float, unsigned long long, long long>(r.g, r.f, r.sbuf[r.smooth & 1], r.scale,
                                                                       r.Z[0], r.Z[1], r.Z[2], dt, p);
             else
-                e_fx_cell(r.g, r.f, r.J[0], r.J[1], r.J[2], r.Z[0], r.Z[1], r.Z[2], dt, r.scale, p);
+                e_fx_cell(r.g, r.f, r.J[0], r.J[1], r.J[2], r.Z[0], r.Z[1], r.Z[2], dt,
+                          F2{(float)r.scale, (float)(r.scale - (double)(float)r.scale)}, p);
         }
     }
 }
@@ -357,7 +391,12 @@ __global__ void k_add_uniform(Geom g, FieldPtrs<R> f, double e0, double e1, doub
         double v[6] = {e0, e1, e2, b0, b1, b2};
         if (g.bcx == 1 && i == 0) { v[1] = 0.0; v[2] = 0.0; v[3] = 0.0; }
         if constexpr (std::is_same<R, float>::value) {
-            for (int c = 0; c < 3; ++c) e_store(f, c, p, __dadd_rn(e_full(f, c, p), v[c]));
+            for (int c = 0; c < 3; ++c) {
+                const double x = __dadd_rn(e_full(f, c, p), v[c]);
+                const float hi = (float)x;
+                f.e[c][p] = hi;
+                f.el[c][p] = (float)(x - (double)hi);
+            }
         } else {
             f.e[0][p] += (R)v[0]; f.e[1][p] += (R)v[1]; f.e[2][p] += (R)v[2];
         }
@@ -399,8 +438,10 @@ void launch_fields_multi(int phase, const FieldRunF *runs_dev, const int *block_
 void launch_e_advance_fx(const Geom &g, FieldPtrs<float> f, const unsigned long long *const J[3],
                          unsigned long long *const Jzero[3], float dt, double alpha_abs, long long *hist_inc,
                          cudaStream_t s) {
+    const double scale = alpha_abs * 0x1p-36;
+    const F2 sc = {(float)scale, (float)(scale - (double)(float)scale)};
     k_e_advance_fx<<<grid_for(g.pcells, 256), 256, 0, s>>>(g, f, J[0], J[1], J[2], Jzero[0], Jzero[1], Jzero[2],
-                                                           dt, alpha_abs * 0x1p-36, hist_inc);
+                                                           dt, sc, hist_inc);
 }
 
 template <typename R, typename ZT, typename CT>

@@ -63,8 +63,8 @@ __host__ __device__ inline void unpack_cell(int ndim, uint32_t c, int &i, int &j
 // Field planes of one run.  el (mixed path only, null in the FP64 path) holds
 // the low-order part of e: the electric field is e + el, carried as an
 // unevaluated FP32 pair so that the FP32 rounding of e does not accumulate
-// over the steps (the e advance updates the pair in FP64 from the exact
-// integer current).  The gather reads e alone.
+// over the steps (the e advance updates the pair with error-free FP32
+// transformations from the exact integer current).  The gather reads e alone.
 template <typename R>
 struct FieldPtrs {
     R *e[3];
@@ -78,13 +78,6 @@ __device__ inline double e_full(const FieldPtrs<R> &f, int c, long long p) {
     double v = (double)f.e[c][p];
     if (f.el[c]) v += (double)f.el[c][p];
     return v;
-}
-
-// Store an FP64 value of e as its FP32 pair (high part, exact remainder rounded to FP32).
-__device__ inline void e_store(const FieldPtrs<float> &f, int c, long long p, double v) {
-    const float hi = (float)v;
-    f.e[c][p] = hi;
-    f.el[c][p] = (float)(v - (double)hi);
 }
 
 struct Species64 {

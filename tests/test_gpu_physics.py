@@ -74,11 +74,11 @@ def test_filamentation_growth_rate_mixed_matches_fp64(runs):
     assert abs(dmx / d64 - 1) <= 0.05, (dmx, d64)
 
 
-def _linear_phase_rate(e, dt):
+def _linear_phase_rate(e, dt, floor_at=(20, 40)):
     """Growth rate of one mode's energy over its linear phase: from the first
-    time it exceeds 10x its noise floor (median of steps 20-40) to the first
-    time it reaches 10 % of its maximum; None without 2 decades of growth."""
-    floor, peak = np.median(e[20:40]), e.max()
+    time it exceeds 10x its noise floor (median of samples floor_at) to the
+    first time it reaches 10 % of its maximum; None without 2 decades of growth."""
+    floor, peak = np.median(e[floor_at[0]:floor_at[1]]), e.max()
     if peak < 100 * floor:
         return None
     i1 = int(np.argmax(e > 10 * floor))
@@ -128,6 +128,65 @@ def test_filamentation_fastest_mode_grows_at_the_cold_rate():
     assert abs(rates["mixed"] / rates["fp64"] - 1) <= 0.05, rates
     for name in rates:
         assert abs(rates[name] / d_th - 1) <= 0.20, (name, rates[name], d_th)
+
+
+def test_filamentation_at_the_configured_size_grows_at_the_cold_rate():
+    """The filamentation workload as configured (Sect. 3.2.1, Table two_stream's
+    resolution): 1024^2 cells, 20 cells per c/omega_pe (51.2 skin depths),
+    electrons 25 + 25 per cell in the two beams (Gamma0 = 3, theta = 0.01),
+    positrons 50 per cell at rest (theta = 0.01) on the electrons, 2000 steps
+    of the mixed path (7.96 plasma periods).  The fastest-growing shell of
+    in-plane magnetic modes grows within 15 % of the cold rate beta0 omega_pe /
+    sqrt(Gamma0), i.e. its e-folding time is within 15 % of 0.292 T_pe (the
+    paper measures 6-14 % at this resolution; measured here 0.86 of the rate,
+    stable between 0.85 and 0.88 over reasonable fit windows: the thermal
+    spread of the beams lowers the fastest rate below the cold limit).  The
+    long-wavelength shells match the cold rate at their own k within 10 %
+    (measured 0.91-0.93).  The box's magnetic energy saturates within the run
+    and charge stays conserved to 1e-6 of max rho."""
+    nx, n_x, ppc, steps, every, nshell = 1024, 20.0, 25, 2000, 4, 64
+    n = ppc * nx * nx
+    d = pic.run_desc(2, nx, nx, 1, n_x, 4.0 * ppc, DT, [(-1.0, 1.0, n), (1.0, 1.0, 2 * n), (-1.0, 1.0, n)])
+    omega_pe = 1.0 / n_x          # all electrons (50 per cell = rho_sp0 / 2)
+    d_th = BETA0 * omega_pe / np.sqrt(3.0)
+    with pic.Context([d], precision=pic.PIC_MIXED) as ctx:
+        ctx.load_maxwell_juttner(0, 0, ppc, 0.01, (0.0, 0.0, BETA0), seed=3)
+        ctx.load_maxwell_juttner(0, 2, ppc, 0.01, (0.0, 0.0, -BETA0), seed=4)
+        # positrons at rest on top of both beams (species 1 holds 2 ppc: loaded from beam 1, then its
+        # second half re-seated on beam 2 through a state round trip)
+        ctx.load_maxwell_juttner(0, 1, 2 * ppc, 0.01, (0.0, 0.0, 0.0), seed=5)
+        f, p, _ = ctx.get_state(0)
+        p[1][:3, :n] = p[0][:3]
+        p[1][:3, n:] = p[2][:3]
+        ctx.set_state(0, f, p)
+        shells = []
+        for k in range(0, 1400, every):
+            ctx.step(every)
+            fb, _, _ = ctx.get_state(0, fields_only=True)
+            shells.append(_shell_energy(fb[3:5], nshell))
+        ctx.step(steps - 1400)
+        dg = ctx.diagnostics(0)
+        hist = ctx.energy_history(0)
+    shells = np.array(shells)
+    rates = {q: _linear_phase_rate(shells[:, q], every * DT, floor_at=(5, 10)) for q in range(1, nshell)}
+    best = max(r for r in rates.values() if r)
+    print("configured filamentation: fastest-shell rate %.5f, cold rate %.5f (ratio %.3f); tau = %.3f T_pe" %
+          (best, d_th, best / d_th, 1.0 / (2 * np.pi * best / omega_pe)))
+    assert abs(best / d_th - 1) <= 0.15, (best, d_th)
+    # the long-wavelength shells (k c/omega_pe < 3) follow the cold rate at their own k (finite-k
+    # cold two-fluid relation) within 10 %: thermal spread matters only at larger k
+    pops = [(0.5, BETA0, 3.0), (0.5, BETA0, 3.0), (1.0, 0.0, 1.0)]
+    for q in (1, 2, 3):
+        kc = (q + 0.5) / nshell * np.pi * n_x          # shell centre, k c / omega_pe
+        d_k = theory.filamentation_rate_cold(kc, pops) * omega_pe
+        print("shell %d (k c/omega_pe = %.2f): rate %.5f, finite-k cold rate %.5f (ratio %.3f)" %
+              (q, kc, rates[q], d_k, rates[q] / d_k))
+        assert abs(rates[q] / d_k - 1) <= 0.10, (q, rates[q], d_k)
+    eb = hist[:, 2]
+    assert eb.max() > 1e3 * eb[20]                                # grew by more than three decades
+    late = np.log(eb[-1] / eb[-400]) / (2 * 400 * DT)             # field growth rate over the last 400 steps
+    assert late < 0.3 * d_th, late                                # ... and saturated
+    assert dg["gauss_max"] <= 1e-6 * dg["rho_max"], dg
 
 
 def test_filamentation_growth_rate_fp64_matches_oracle(runs):
@@ -263,6 +322,109 @@ def test_harris_sheet_tearing_grows_at_the_same_rate_in_both_paths():
             print("tearing %s: tau = %.2f T_pe (paper: 2.5 T_pe at n_x = 15)" % (name, 1.0 / r / T_pe))
     assert rates["fp64"] and rates["mixed"], rates
     assert abs(rates["mixed"] / rates["fp64"] - 1) <= 0.10, rates
+
+
+HARRIS = dict(theta=1.0, GU=0.68, wce=1.82, l_over_de=1.62, n_x=4.0, ppc=16, nx=64, ny=128)
+
+
+def _harris_desc(mu):
+    h = HARRIS
+    L = h["l_over_de"] * h["n_x"]
+    cap = int(h["ppc"] * 2.2 * L * h["ny"]) + 1024
+    return pic.run_desc(2, h["nx"], h["ny"], 1, h["n_x"], 2.0 * h["ppc"], DT, [(-1.0, 1.0, cap), (1.0, mu, cap)],
+                        bc=(1, 0, 0))
+
+
+def _harris_load(ctx, mu, method, seeds):
+    """Electrons drifting along -z and ions (or positrons) along +z with Gamma U
+    = 0.68 and equal temperatures (App. C: Theta_i = Theta_e m_e/m_i, Gamma_i U_i
+    = -Gamma_e U_e), sech^2 profile, B_y = B0 tanh((x - x0)/L) with the Table
+    tearing relations for Theta = 1 (omega_ce/omega_pe = 1.82, L = 1.62 d_e)."""
+    h = HARRIS
+    L, x0 = h["l_over_de"] * h["n_x"], h["nx"] / 2.0
+    beta = h["GU"] / np.sqrt(1.0 + h["GU"] ** 2)
+    ctx.load_maxwell_juttner(0, 0, h["ppc"], h["theta"], (0.0, 0.0, -beta), profile=pic.PIC_PROFILE_HARRIS,
+                             profile_params=(L, x0), method=method, seed=seeds[0])
+    ctx.load_maxwell_juttner(0, 1, h["ppc"], h["theta"] / mu, (0.0, 0.0, beta), profile=pic.PIC_PROFILE_HARRIS,
+                             profile_params=(L, x0), colocate_with=0, method=method, seed=seeds[1])
+    f, p, _ = ctx.get_state(0)
+    i = np.arange(h["nx"])
+    f[4, 0, :, :] = h["wce"] / h["n_x"] * np.tanh((i[None, :] + 0.5 - x0) / L)    # b_y at (i + 1/2, j)
+    ctx.set_state(0, f, p)
+    return f, p
+
+
+def _run_ebx(ctx, nsteps):
+    e = np.zeros(nsteps)
+    for k in range(nsteps):
+        ctx.step(1)
+        g, _, _ = ctx.get_state(0, fields_only=True)
+        e[k] = (g[3] ** 2).sum()
+    return e
+
+
+@pytest.mark.parametrize("mu,nsteps", [(1.0, 1000), (25.0, 1400)])
+def test_harris_tearing_matches_oracle_from_the_same_state(mu, nsteps):
+    """Config 5 (Sect. 3.4, App. C) at reduced size: a relativistic Harris sheet
+    of pairs (mu = m_i/m_e = 1) or of ions and electrons at equal temperature
+    (mu = 25) between conducting walls, 64 x 128 cells, 4 cells per d_e, 16
+    particles per cell per species at the sheet centre.  From one loaded state,
+    the oracle, the FP64 path and the mixed path run side by side; the tearing
+    mode grows out of the particle noise (b_x energy up by more than 1.5
+    decades in the linear phase).  The FP64 path's E_bx equals the oracle's at
+    every step to 1e-6 relative through step 800 (measured 2e-8 and 1e-7; the
+    runs separate only once the sheet has torn), and the growth rates of both
+    GPU paths equal the oracle's, FP64 to 1e-6 and mixed to 1 % (measured 1e-10
+    and 8e-4).  The oracle runs as its OpenMP build (the same arithmetic; only
+    the order of the FP64 current sums differs, as it does on the GPU)."""
+    d = _harris_desc(mu)
+    with pic.Context([d], precision=pic.PIC_FP64) as ctx:
+        f, p = _harris_load(ctx, mu, pic.PIC_MJ_EXACT, (41, 42))
+    st = oracle.State.empty(2, d.nx, d.ny, 1, DT, d.n_x, d.rho_sp0, bc_x=oracle.BC_CONDUCTOR)
+    st.e[:] = f[:3]
+    st.b[:] = f[3:]
+    st.species.append(oracle.Species(p[0][:3].copy(), p[0][3:].copy(), -1.0, 1.0))
+    st.species.append(oracle.Species(p[1][:3].copy(), p[1][3:].copy(), 1.0, mu))
+    e_orc = np.zeros(nsteps)
+    for k in range(nsteps):
+        oracle.step_parallel(st, 1)
+        e_orc[k] = (st.b[0] ** 2).sum()
+    runs = {}
+    for name, prec in (("fp64", pic.PIC_FP64), ("mixed", pic.PIC_MIXED)):
+        with pic.Context([d], precision=prec) as ctx:
+            ctx.set_state(0, f, p)
+            runs[name] = _run_ebx(ctx, nsteps)
+    ok = e_orc[:800] > 0
+    rel = np.abs(runs["fp64"][:800] - e_orc[:800])[ok] / e_orc[:800][ok]
+    r_orc = _linear_phase_rate(e_orc, DT)
+    r64, rmx = _linear_phase_rate(runs["fp64"], DT), _linear_phase_rate(runs["mixed"], DT)
+    print("tearing mu=%g: max |E_bx fp64 - oracle|/oracle over 800 steps %.2e; rates oracle %.6f fp64 %.6f mixed %.6f"
+          % (mu, rel.max(), r_orc, r64, rmx))
+    assert rel.max() <= 1e-6, rel.max()
+    assert r_orc and r64 and rmx
+    assert abs(r64 / r_orc - 1) <= 1e-6 and abs(rmx / r_orc - 1) <= 0.01, (r_orc, r64, rmx)
+
+
+@pytest.mark.parametrize("mu,nsteps", [(1.0, 1000), (25.0, 1400)])
+def test_harris_sheet_loaded_by_the_learned_sampler_tears_like_the_exact_loader(mu, nsteps):
+    """Config 5 with the learned loader (the brief's pattern 4): the same Harris
+    sheet (pairs, and ions of m_i/m_e = 25 at Theta_i = 0.04) loaded on the GPU
+    by the trained network (FP16 inference) and by the exact inversion, with
+    the same random streams, then advanced by the mixed path.  The tearing
+    growth rates agree within 5 % (measured 1 %); sheets loaded with other
+    seeds differ by about 18 %, so the learned sampler reproduces the exact
+    loader's realisation, not only its statistics."""
+    d = _harris_desc(mu)
+    rates = {}
+    for tag, method in (("exact", pic.PIC_MJ_EXACT), ("mlp", pic.PIC_MJ_MLP)):
+        with pic.Context([d], precision=pic.PIC_MIXED) as ctx:
+            if method == pic.PIC_MJ_MLP:
+                ctx.mlp_train(steps=12000, batch=8192, lr=3e-3, seed=1)
+            _harris_load(ctx, mu, method, (51, 52))
+            rates[tag] = _linear_phase_rate(_run_ebx(ctx, nsteps), DT)
+    print("tearing mu=%g by loader: exact %s mlp %s" % (mu, rates["exact"], rates["mlp"]))
+    assert rates["exact"] and rates["mlp"]
+    assert abs(rates["mlp"] / rates["exact"] - 1) <= 0.05, rates
 
 
 def test_ensemble_field_fluctuation_level_scales_as_one_over_ppc():

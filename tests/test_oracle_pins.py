@@ -663,3 +663,28 @@ def test_filament_scale_of_gaussian_filaments_is_the_closed_form():
     cur[2] = amp[None]                         # J_z filaments, constant along z
     expect = 5.0 * 2.0 * s * np.sqrt(np.log(1.25))
     assert abs(filaments.filament_scale(cur) / expect - 1) <= 0.05
+
+
+def test_openmp_build_of_the_oracle_equals_the_plain_build():
+    """The all-cores timing build (particle loop shared between threads, one
+    current grid per thread) gives the plain oracle's step up to the order of
+    the FP64 current sums."""
+    import synth
+    arr = synth.random_state_arrays(3, 3, 12, 10, 8, ppc=6, spread=0.5, amp_e=0.02, amp_b=0.02, colocate=False)
+
+    def make():
+        st = oracle.State.empty(3, 12, 10, 8, 0.5, 2.0, 12.0)
+        st.e[:] = arr["e"]
+        st.b[:] = arr["b"]
+        for sp in arr["species"]:
+            st.species.append(oracle.Species(sp["pos"].copy(), sp["u"].copy(), sp["q_over_e"], sp["m_over_me"]))
+        return st
+    a, b = make(), make()
+    oracle.step(a, 3)
+    threads = oracle.step_parallel(b, 3, 4)
+    assert threads >= 1
+    assert np.abs(a.e - b.e).max() <= 1e-13 * np.abs(a.e).max()
+    for sa, sb in zip(a.species, b.species):
+        assert np.abs(sa.pos - sb.pos).max() <= 1e-12
+        assert np.abs(sa.u - sb.u).max() <= 1e-13 * np.abs(sa.u).max()
+
