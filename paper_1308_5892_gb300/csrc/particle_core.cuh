@@ -14,6 +14,11 @@ template <> __device__ inline double rsqrt_<double>(double x) { return 1.0 / sqr
 // Division: IEEE in FP64; in FP32 the fast reciprocal-based quotient (2 ulp for
 // divisors in [2^-126, 2^126], which every divisor here is), far below the
 // FP32 rounding of the arguments themselves.
+// Fused multiply-add with one rounding, written out so that the breakpoints of
+// a path do not depend on the compiler's choice to contract or not.
+template <typename R> __device__ inline R fma_(R a, R b, R c);
+template <> __device__ inline float fma_<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ inline double fma_<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <typename R> __device__ inline R div_(R a, R b);
 template <> __device__ inline float div_<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ inline double div_<double>(double a, double b) { return a / b; }
@@ -114,6 +119,10 @@ __device__ __forceinline__ void deposit_segment(const R d[3], const R D[3], R al
 // init() sets up the split; piece(k, ...) must then be called for k = 0, 1, ...,
 // ncross in this order and returns piece k: its cell offset from the start
 // cell, its start offset and its displacement.
+// Both are written without data-dependent branches (every candidate value is
+// computed and the right one selected), so the lanes of a warp whose particles
+// cross different planes stay converged; the arithmetic of each value is the
+// same as that of the branching form.
 template <int NDIM, typename R>
 struct PathSplit {
     R cur[3], dv[3], tc[3], d1[3];
@@ -122,41 +131,35 @@ struct PathSplit {
     R tprev, dz;
     __device__ __forceinline__ int sh(int a) const { return ((code >> (4 * a)) & 3) - 1; }
     __device__ __forceinline__ int rk(int a) const { return (code >> (4 * a + 2)) & 3; }
-    __device__ __forceinline__ R plo(int a) const { return sh(a) > 0 ? R(1) : R(0); }   // plane, start-cell coords
-    __device__ __forceinline__ R pnew(int a) const { return sh(a) > 0 ? R(0) : R(1); }  // same plane, end-cell coords
     __device__ __forceinline__ void init(const R d0[3], const int s[3], const R d1_[3], R dz2d) {
         ncross = 0;
         code = 0;
+        bool cr[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             cur[a] = a < NDIM ? d0[a] : R(0);
             d1[a] = a < NDIM ? d1_[a] : R(0);
-            tc[a] = R(2);
-            dv[a] = R(0);
             const int sa = a < NDIM ? s[a] : 0;
             code |= (sa + 1) << (4 * a);
-            if (a < NDIM) {
-                if (sa != 0) {
-                    const R first = (sa > 0 ? R(1) : R(0)) - cur[a];
-                    dv[a] = first + (d1[a] - (sa > 0 ? R(0) : R(1)));
-                    tc[a] = dv[a] != R(0) ? div_<R>(first, dv[a]) : R(0);
-                    ++ncross;
-                } else {
-                    dv[a] = d1[a] - cur[a];
-                }
-            }
+            cr[a] = a < NDIM && sa != 0;
+            // crossing: the plane in start-cell coordinates, then the rest in end-cell coordinates
+            const R plane = sa > 0 ? R(1) : R(0), pn = sa > 0 ? R(0) : R(1);
+            const R first = plane - cur[a];
+            const R dv_cross = first + (d1[a] - pn);
+            const R q = div_<R>(first, dv_cross);   // unused (selected away) when the axis is not crossed
+            dv[a] = a < NDIM ? (cr[a] ? dv_cross : d1[a] - cur[a]) : R(0);
+            tc[a] = cr[a] ? (dv_cross != R(0) ? q : R(0)) : R(2);
+            ncross += cr[a] ? 1 : 0;
         }
-        // rank of each crossing among the crossings, ties by axis order
+        // rank of each crossing among the crossings, ties by axis order (an axis
+        // that is not crossed has tc = 2 and never counts below a crossing)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            int r = 3;
-            if (a < NDIM && sh(a) != 0) {
-                r = 0;
+            int r = 0;
 #pragma unroll
-                for (int b = 0; b < NDIM; ++b)
-                    if (b != a && sh(b) != 0 && (tc[b] < tc[a] || (tc[b] == tc[a] && b < a))) ++r;
-            }
-            code |= r << (4 * a + 2);
+            for (int b = 0; b < 3; ++b)
+                if (b != a) r += (tc[b] < tc[a] || (tc[b] == tc[a] && b < a)) ? 1 : 0;
+            code |= (cr[a] ? r : 3) << (4 * a + 2);
         }
         tprev = R(0);
         dz = dz2d;
@@ -164,22 +167,21 @@ struct PathSplit {
     __device__ __forceinline__ void piece(int k, int c[3], R d[3], R D[3]) {
         R tn = R(1);
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a)
-            if (rk(a) == k) tn = tc[a];
+        for (int a = 0; a < NDIM; ++a) tn = rk(a) == k ? tc[a] : tn;
         const bool last = (k == ncross);
+        const R dt = tn - tprev;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            c[a] = rk(a) < k ? sh(a) : 0;
+            const int ra = rk(a), sa = sh(a);
+            c[a] = ra < k ? sa : 0;
             d[a] = cur[a];
             if (a >= NDIM) { D[a] = R(0); continue; }
-            R endp;
-            if (rk(a) == k) endp = plo(a);
-            else if (last) endp = d1[a];
-            else endp = snap_offset<R>(cur[a] + dv[a] * (tn - tprev));
+            const R mid = snap_offset<R>(fma_<R>(dv[a], dt, cur[a]));
+            const R endp = ra == k ? (sa > 0 ? R(1) : R(0)) : (last ? d1[a] : mid);
             D[a] = endp - cur[a];
-            cur[a] = rk(a) == k ? pnew(a) : endp;
+            cur[a] = ra == k ? (sa > 0 ? R(0) : R(1)) : endp;
         }
-        if (NDIM == 2) D[2] = dz * (tn - tprev);
+        if (NDIM == 2) D[2] = dz * dt;
         tprev = tn;
     }
 };
