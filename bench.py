@@ -349,7 +349,66 @@ def run_ours(args, w):
         e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     if args.no_fp64:
         results["fp64"] = None
-    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, len(descs), alu)
+    ens = None
+    if members is None and not args.no_ensemble:
+        ens = _ensemble_leg(pic, torch, args, seed, barrier, dist)
+    return _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, len(descs), alu, ens)
+
+
+def _ensemble_leg(pic, torch, args, seed, barrier, dist):
+    """The batched ensemble of 256 uneven 2D3V runs (ensemble256) as a second leg
+    of the default line: autotuned, then a window of graph-replayed steps (the
+    value) and a window of direct launches with CUDA events around the batched
+    push kernel (its roofline)."""
+    w = WORKLOADS["ensemble256"]
+    members = ensemble_members(w["ensemble"])
+    descs, npart = [], 0
+    for m in members:
+        n = m["ppc"] * m["nx"] * m["ny"]
+        npart += 2 * n
+        descs.append(pic.run_desc(2, m["nx"], m["ny"], 1, m["n_x"], m["rho_sp0"], w["dt"],
+                                  [(-1.0, 1.0, n), (1.0, 1.0, n)]))
+    ctx = pic.Context(descs, precision=pic.PIC_MIXED)
+    for r, m in enumerate(members):
+        ctx.load_maxwell_juttner(r, 0, m["ppc"], m["theta"], (0.0, 0.0, 0.0), seed=seed + 2 * r)
+        ctx.load_maxwell_juttner(r, 1, m["ppc"], m["theta"], (0.0, 0.0, 0.0), colocate_with=0, seed=seed + 2 * r + 1)
+    tuned = None if args.no_autotune else ctx.autotune(max_steps=args.autotune_steps)
+    steps = args.ensemble_steps
+    K = int(ctx.tuning()["sort_interval"])
+    ctx.set_flags(0)
+    ctx.step(max(args.warmup, 2 * K))
+    stream = torch.cuda.current_stream()
+
+    def window(flags):
+        ctx.set_flags(flags)
+        ctx.kernel_time(pic.PIC_KERNEL_PUSH, reset=True)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(steps)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    ms = max_over_ranks(window(0), dist, "cuda")
+    window(pic.PIC_FLAG_TIMING)
+    push_ms, push_n = ctx.kernel_time(pic.PIC_KERNEL_PUSH)
+    launches = ctx.counters()["launches_per_step"]
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    world = dist.get_world_size() if dist is not None else 1
+    peak, peak_kind = _peaks()
+    push_step = push_ms / max(push_n, 1) if push_n else None
+    ach = 48.0 * npart / (push_step * 1e-3) / 1e9 if push_step else None
+    return {"workload": w["name"], "runs": len(members), "particles_per_gpu": npart, "steps": steps,
+            "value": job_value(npart, steps, ms, world), "unit": "particle-steps/ns", "ms_per_step": ms / steps,
+            "tuning": tuned, "launches_per_step": launches,
+            "roofline": None if ach is None else {
+                "bound": "hbm", "kernel": "k_push_mixed_multi (all runs, one persistent launch)", "achieved": ach,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                "push_ms_per_step": push_step, "bytes_per_particle_step": 48.0}}
 
 
 def _e2e(pic, torch, desc, w, seed, args, barrier):
@@ -390,10 +449,12 @@ FP64_INST_PER_PARTICLE = {3: 274.0, 2: 170.0}
 # 103.3 per particle, ncu on the 64^3 workload)
 MIXED_FP32_FLOPS_PER_PARTICLE = {3: 331.8}
 # DRAM bytes (read + written) per particle-step of the 3D push kernel, from one
-# ncu capture of the same kernel and tiling on the 64^3 case (profiles/
-# push_mixed_thermal3d_64.md: 917.4 MB for 16,777,216 particles), scaled to a
-# launch by the particles it processes.  None where no capture exists.
-PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.4e6 / 16777216}
+# ncu capture of the same kernel and tiling (16x8x4, sort interval 3) on the
+# 64^3 case (profiles/push_mixed_thermal3d_64.md: 917.3 MB for 16,777,216
+# particles), scaled to a launch by the particles it processes.  None where no
+# capture exists.
+PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.3e6 / 16777216}
+PUSH_TRAFFIC_TILING = {3: ([16, 8, 4], 3)}   # (tile, sort interval) of that capture
 
 
 def _fp64_roofline(w, f64, npart, alu, peak_hbm):
@@ -416,7 +477,7 @@ def _fp64_roofline(w, f64, npart, alu, peak_hbm):
     return out
 
 
-def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1, alu=None):
+def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1, alu=None, ensemble=None):
     m = results["mixed"]
     value = job_value(npart, m["steps"], m["ms"], world)
     f64 = results["fp64"]
@@ -439,9 +500,12 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                                               "roofline": _fp64_roofline(w, f64, npart, alu, peak)},
             "alu_peaks": alu,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": (PUSH_TRAFFIC_B_PER_PARTICLE.get(w.get("ndim"), 0.0) * npart
-                                     if w.get("ndim") in PUSH_TRAFFIC_B_PER_PARTICLE and nruns == 1 else None),
-                         "traffic_source": "ncu dram bytes of the same kernel at 64^3, scaled by particles",
+                         # counters of another tiling do not describe this kernel: null then
+                         "traffic": (PUSH_TRAFFIC_B_PER_PARTICLE[w["ndim"]] * npart
+                                     if w.get("ndim") in PUSH_TRAFFIC_B_PER_PARTICLE and nruns == 1
+                                     and PUSH_TRAFFIC_TILING[w["ndim"]] == (list(m["tuning"]["tile"]),
+                                                                            m["tuning"]["sort_interval"]) else None),
+                         "traffic_source": "ncu dram bytes of the same kernel and tiling (16x8x4) at 64^3, scaled by particles",
                          "kernel": "k_push_mixed (gather+push+deposit, both species)",
                          "peak_kind": peak_kind, "push_ms_per_step": push_launch_ms,
                          "field_ms_per_step": m["field_ms"] / m["steps"], "sort_ms_total": m["sort_ms"],
@@ -463,6 +527,8 @@ def _report(args, w, results, npart, world, rank, e2e_s, h2d, d2h, dist, nruns=1
                      "gauss_over_rho_max": m["diag"]["gauss_max"] / max(m["diag"]["rho_max"], 1e-300),
                      "steps_since_load": int(m["diag"]["step"])},
         }
+        if ensemble is not None:
+            out["ensemble"] = ensemble
         if args.smooth > 0:
             # current smoothing: each pass reads and writes 3 x 8 B per interior cell (the in-place
             # fold of the ghost images touches only the boundary layers and is not counted)
@@ -504,6 +570,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--smooth", type=int, default=0, help="current smoothing passes per step (0..4, default off)")
     ap.add_argument("--autotune-steps", type=int, default=120)
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-run ensemble leg of the default line")
+    ap.add_argument("--ensemble-steps", type=int, default=12)
     args = ap.parse_args()
     args.tile = tuple(args.tile)
     w = dict(WORKLOADS[args.workload])

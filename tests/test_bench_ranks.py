@@ -67,7 +67,7 @@ def test_report_line_carries_the_contract_keys():
     import types
     sys.path.insert(0, ROOT)
     import bench
-    args = types.SimpleNamespace(steps=20, warmup=3, no_cpu_baseline=True, smooth=1, gpus=1)
+    args = types.SimpleNamespace(steps=20, warmup=3, no_cpu_baseline=True, smooth=1, gpus=1, no_ensemble=True)
     w = dict(bench.WORKLOADS["thermal3d_128"], smooth=1)
     common = dict(ms_direct=160.0, field_ms=7.0, smooth_ms=1.3, ncell=128 ** 3, clocks={"sm_mhz": 2070.0},
                   diag={"gauss_max": 1e-6, "rho_max": 1.5, "step": 140})
