@@ -562,6 +562,7 @@ pic_status setup_run(pic_ctx *ctx, Run &r, const pic_opts *o) {
     g.G = G; g.Gz = d.ndim == 3 ? G : 0;
     g.px = g.nx + 2 * G; g.py = g.ny + 2 * G; g.pz = g.nz + 2 * g.Gz;
     g.pcells = (long long)g.px * g.py * g.pz;
+    g.set_divisors();
     g.bcx = d.bc[0];
     r.inv_alpha_abs = d.n_x * d.n_x * d.rho_sp0 / 2.0;
     const size_t rs = real_size(ctx);

@@ -20,7 +20,18 @@ namespace pic {
 
 namespace {
 
+// Padded coordinates of padded index p: multiply-high divisions while the
+// grid has fewer than 2^32 padded cells, 64-bit division beyond.
 __device__ inline void padded_coords(const Geom &g, long long p, int &pi, int &pj, int &pk) {
+    if (g.pcells <= 0xffffffffLL) {
+        const uint32_t n = (uint32_t)p;
+        const uint32_t q = g.fpx.div(n);
+        pi = (int)(n - q * (uint32_t)g.px);
+        const uint32_t r = g.fpy.div(q);
+        pj = (int)(q - r * (uint32_t)g.py);
+        pk = (int)r;
+        return;
+    }
     pi = (int)(p % g.px);
     long long q = p / g.px;
     pj = (int)(q % g.py);
@@ -97,24 +108,30 @@ __global__ void k_b_advance(Geom g, FieldPtrs<R> f, R h, HistRef hist) {
     if (energy_acc) block_accumulate<6>(acc, energy_acc);
 }
 
-// Sum of the current over every padded image of interior cell (i,j,k).
+// Padded coordinates of the images of interior coordinate i along one axis
+// (n cells, ghost width G): i + G - n, i + G, i + G + n, those inside [0, n + 2G),
+// in that order; returns their count.
+__device__ __forceinline__ int axis_images(int i, int n, int G, int (&q)[3]) {
+    int c = 0;
+    if (i >= n - G) q[c++] = i + G - n;
+    q[c++] = i + G;
+    if (i < G) q[c++] = i + G + n;
+    return c;
+}
+
+// Sum of the current over every padded image of interior cell (i,j,k), in the
+// order of increasing image offset along z, y, then x.
 template <typename R>
 __device__ inline R folded_current(const Geom &g, const R *J, int i, int j, int k) {
+    int qx[3], qy[3], qz[3];
+    const int nqx = axis_images(i, g.nx, g.G, qx), nqy = axis_images(j, g.ny, g.G, qy);
+    const int nqz = g.ndim == 3 ? axis_images(k, g.nz, g.Gz, qz) : (qz[0] = k + g.Gz, 1);
     R s = R(0);
-    const int zlo = g.ndim == 3 ? -1 : 0, zhi = g.ndim == 3 ? 1 : 0;
-    for (int mz = zlo; mz <= zhi; ++mz) {
-        const int qk = k + g.Gz + mz * g.nz;
-        if (qk < 0 || qk >= g.pz) continue;
-        for (int my = -1; my <= 1; ++my) {
-            const int qj = j + g.G + my * g.ny;
-            if (qj < 0 || qj >= g.py) continue;
-            for (int mx = -1; mx <= 1; ++mx) {
-                const int qi = i + g.G + mx * g.nx;
-                if (qi < 0 || qi >= g.px) continue;
-                s += J[((long long)qk * g.py + qj) * g.px + qi];
-            }
+    for (int c = 0; c < nqz; ++c)
+        for (int b = 0; b < nqy; ++b) {
+            const long long row = ((long long)qz[c] * g.py + qy[b]) * g.px;
+            for (int a = 0; a < nqx; ++a) s += J[row + qx[a]];
         }
-    }
     return s;
 }
 

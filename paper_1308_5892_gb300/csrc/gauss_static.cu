@@ -105,6 +105,7 @@ extern "C" pic_status pic_gauss_residual_static(int ndim, int nx, int ny, int nz
     g.G = 0; g.Gz = 0;
     g.px = nx; g.py = ny; g.pz = nz;
     g.pcells = ncell;
+    g.set_divisors();
     g.bcx = 0;
     // out[0] = max |div e - rho~|, out[1] = max over species of max |rho~_s|
     k_zero_d<<<1, 32, 0, s>>>(out, 2);

@@ -35,18 +35,53 @@ enum : int {
     ERR_RANGE = 16,      // a particle position outside the domain (state upload)
 };
 
+// Unsigned 32-bit division by a divisor fixed at set-up, through a
+// multiply-high (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d)
+// + 1, n / d = (t + ((n - t) >> 1)) >> (l - 1) with t = mulhi(m, n), for every
+// n < 2^32 and d >= 2.  A hardware division takes tens of instructions.
+struct FastDiv {
+    uint32_t d, m, l;
+    __host__ void init(uint32_t dv) {
+        d = dv < 1 ? 1 : dv;
+        l = 0;
+        while (l < 32 && (1ull << l) < d) ++l;
+        m = d == 1 ? 0u : (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        if (d == 1) return n;
+        const uint32_t t = __umulhi(m, n);
+        return (t + ((n - t) >> 1)) >> (l - 1);
+    }
+};
+
+// Periodic wrap into [0, n): arguments within one period of the range (all
+// the stencils and ghosts here) take two comparisons, others the modulo.
+__host__ __device__ inline int wrap_index(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;
+    if (i < 0 && i >= -n) return i + n;
+    if (i >= n && i < 2 * n) return i - n;
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
 struct Geom {
     int ndim, nx, ny, nz;
     int G, Gz;            // ghost width in x,y and in z (0 in 2D)
     int px, py, pz;       // padded extents
     long long pcells;     // px*py*pz
     int bcx;              // 0 periodic, 1 conductor walls at x = 0, nx
+    FastDiv fpx, fpy;     // division by px and py (set_divisors)
+    __host__ void set_divisors() {
+        fpx.init((uint32_t)px);
+        fpy.init((uint32_t)py);
+    }
     __host__ __device__ inline long long pidx(int i, int j, int k) const {
         return ((long long)(k + Gz) * py + (j + G)) * px + (i + G);
     }
-    __host__ __device__ inline int wx(int i) const { int r = i % nx; return r < 0 ? r + nx : r; }
-    __host__ __device__ inline int wy(int j) const { int r = j % ny; return r < 0 ? r + ny : r; }
-    __host__ __device__ inline int wz(int k) const { int r = k % nz; return r < 0 ? r + nz : r; }
+    __host__ __device__ inline int wx(int i) const { return wrap_index(i, nx); }
+    __host__ __device__ inline int wy(int j) const { return wrap_index(j, ny); }
+    __host__ __device__ inline int wz(int k) const { return wrap_index(k, nz); }
     // padded index of the interior image of any integer coordinate
     __host__ __device__ inline long long widx(int i, int j, int k) const { return pidx(wx(i), wy(j), wz(k)); }
 };
