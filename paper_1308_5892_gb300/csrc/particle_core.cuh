@@ -6,6 +6,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace pic {
 
 template <typename R> __device__ inline R rsqrt_(R x);
@@ -118,13 +120,17 @@ __device__ __forceinline__ void deposit_segment(const R d[3], const R D[3], R al
 // proportion to their parameter length.
 // init() sets up the split; piece(k, ...) must then be called for k = 0, 1, ...,
 // ncross in this order and returns piece k: its cell offset from the start
-// cell, its start offset and its displacement.
-// Both are written without data-dependent branches (every candidate value is
-// computed and the right one selected), so the lanes of a warp whose particles
-// cross different planes stay converged; the arithmetic of each value is the
-// same as that of the branching form.
+// cell, its start offset and its displacement.  Two forms compute each value
+// by the same arithmetic:
+//  - PathSplitSelect (FP32, the mixed path's warps) has no data-dependent
+//    branches: every candidate value is computed and the right one selected,
+//    so the lanes of a warp whose particles cross different planes stay
+//    converged;
+//  - PathSplitBranch (FP64, one thread per particle, bound by GB300's FP64
+//    pipe and its registers) branches, skipping the work of the axes that are
+//    not crossed.
 template <int NDIM, typename R>
-struct PathSplit {
+struct PathSplitSelect {
     R cur[3], dv[3], tc[3], d1[3];
     int code;     // per axis a, bits 4a..4a+3: (s[a] + 1) | rank[a] << 2, rank 3 if the axis is not crossed
     int ncross;
@@ -146,7 +152,7 @@ struct PathSplit {
             const R plane = sa > 0 ? R(1) : R(0), pn = sa > 0 ? R(0) : R(1);
             const R first = plane - cur[a];
             const R dv_cross = first + (d1[a] - pn);
-            const R q = div_<R>(first, dv_cross);   // unused (selected away) when the axis is not crossed
+            const R q = div_<R>(first, dv_cross);   // selected away when the axis is not crossed
             dv[a] = a < NDIM ? (cr[a] ? dv_cross : d1[a] - cur[a]) : R(0);
             tc[a] = cr[a] ? (dv_cross != R(0) ? q : R(0)) : R(2);
             ncross += cr[a] ? 1 : 0;
@@ -185,6 +191,81 @@ struct PathSplit {
         tprev = tn;
     }
 };
+
+template <int NDIM, typename R>
+struct PathSplitBranch {
+    R cur[3], dv[3], tc[3], d1[3];
+    int code;     // per axis a, bits 4a..4a+3: (s[a] + 1) | rank[a] << 2, rank 3 if the axis is not crossed
+    int ncross;
+    R tprev, dz;
+    __device__ __forceinline__ int sh(int a) const { return ((code >> (4 * a)) & 3) - 1; }
+    __device__ __forceinline__ int rk(int a) const { return (code >> (4 * a + 2)) & 3; }
+    __device__ __forceinline__ R plo(int a) const { return sh(a) > 0 ? R(1) : R(0); }   // plane, start-cell coords
+    __device__ __forceinline__ R pnew(int a) const { return sh(a) > 0 ? R(0) : R(1); }  // same plane, end-cell coords
+    __device__ __forceinline__ void init(const R d0[3], const int s[3], const R d1_[3], R dz2d) {
+        ncross = 0;
+        code = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cur[a] = a < NDIM ? d0[a] : R(0);
+            d1[a] = a < NDIM ? d1_[a] : R(0);
+            tc[a] = R(2);
+            dv[a] = R(0);
+            const int sa = a < NDIM ? s[a] : 0;
+            code |= (sa + 1) << (4 * a);
+            if (a < NDIM) {
+                if (sa != 0) {
+                    const R first = (sa > 0 ? R(1) : R(0)) - cur[a];
+                    dv[a] = first + (d1[a] - (sa > 0 ? R(0) : R(1)));
+                    tc[a] = dv[a] != R(0) ? div_<R>(first, dv[a]) : R(0);
+                    ++ncross;
+                } else {
+                    dv[a] = d1[a] - cur[a];
+                }
+            }
+        }
+        // rank of each crossing among the crossings, ties by axis order
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int r = 3;
+            if (a < NDIM && sh(a) != 0) {
+                r = 0;
+#pragma unroll
+                for (int b = 0; b < NDIM; ++b)
+                    if (b != a && sh(b) != 0 && (tc[b] < tc[a] || (tc[b] == tc[a] && b < a))) ++r;
+            }
+            code |= r << (4 * a + 2);
+        }
+        tprev = R(0);
+        dz = dz2d;
+    }
+    __device__ __forceinline__ void piece(int k, int c[3], R d[3], R D[3]) {
+        R tn = R(1);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a)
+            if (rk(a) == k) tn = tc[a];
+        const bool last = (k == ncross);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            c[a] = rk(a) < k ? sh(a) : 0;
+            d[a] = cur[a];
+            if (a >= NDIM) { D[a] = R(0); continue; }
+            R endp;
+            if (rk(a) == k) endp = plo(a);
+            else if (last) endp = d1[a];
+            else endp = snap_offset<R>(cur[a] + dv[a] * (tn - tprev));
+            D[a] = endp - cur[a];
+            cur[a] = rk(a) == k ? pnew(a) : endp;
+        }
+        if (NDIM == 2) D[2] = dz * (tn - tprev);
+        tprev = tn;
+    }
+};
+
+
+template <int NDIM, typename R>
+using PathSplit = typename std::conditional<sizeof(R) == sizeof(float), PathSplitSelect<NDIM, R>,
+                                            PathSplitBranch<NDIM, R>>::type;
 
 // All pieces of the path, in order: sink.piece(k, di, dj, dk, d, D, alpha).
 template <int NDIM, typename R, class Sink>

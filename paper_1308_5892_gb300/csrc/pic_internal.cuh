@@ -56,13 +56,12 @@ struct FastDiv {
 };
 
 // Periodic wrap into [0, n): arguments within one period of the range (all
-// the stencils and ghosts here) take two comparisons, others the modulo.
+// the stencils and ghosts here) take two selects, others the modulo.
 __host__ __device__ inline int wrap_index(int i, int n) {
-    if ((unsigned)i < (unsigned)n) return i;
-    if (i < 0 && i >= -n) return i + n;
-    if (i >= n && i < 2 * n) return i - n;
-    const int r = i % n;
-    return r < 0 ? r + n : r;
+    const int r = i + (i < 0 ? n : 0) - (i >= n ? n : 0);
+    if ((unsigned)r < (unsigned)n) return r;
+    const int m = i % n;
+    return m < 0 ? m + n : m;
 }
 
 struct Geom {
@@ -84,6 +83,15 @@ struct Geom {
     __host__ __device__ inline int wz(int k) const { return wrap_index(k, nz); }
     // padded index of the interior image of any integer coordinate
     __host__ __device__ inline long long widx(int i, int j, int k) const { return pidx(wx(i), wy(j), wz(k)); }
+    // the same with plain modulo wraps: smaller code where a kernel makes many such
+    // calls and registers are short (the FP64 push kernel spills with the selects)
+    __host__ __device__ inline long long widx_mod(int i, int j, int k) const {
+        int a = i % nx, b = j % ny, c = k % nz;
+        a += a < 0 ? nx : 0;
+        b += b < 0 ? ny : 0;
+        c += c < 0 ? nz : 0;
+        return pidx(a, b, c);
+    }
 };
 
 // Packed cell coordinates of the mixed path: 2D i | j<<16; 3D i | j<<11 | k<<22.

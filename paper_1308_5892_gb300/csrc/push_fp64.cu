@@ -21,7 +21,7 @@ struct GlobalSink64 {
     int ci, cj, ck, oi, oj, ok;
     __device__ void set_cell(int di, int dj, int dk) { oi = ci + di; oj = cj + dj; ok = ck + dk; }
     __device__ void operator()(int comp, int di, int dj, int dk, double v) {
-        atomicAdd(J[comp] + g->widx(oi + di, oj + dj, ok + dk), v);
+        atomicAdd(J[comp] + g->widx_mod(oi + di, oj + dj, ok + dk), v);
     }
 };
 
@@ -30,7 +30,7 @@ __device__ inline double sval64(const Geom &g, const double *a, bool xstag, int 
         if (xstag) { if (i < 0 || i > g.nx - 1) return 0.0; }
         else { if (i <= 0 || i >= g.nx) return 0.0; }
     }
-    return __ldg(a + g.widx(i, j, k));
+    return __ldg(a + g.widx_mod(i, j, k));
 }
 
 // Node-averaged fields at node (i,j,k) (App. A.3.3).
@@ -74,7 +74,7 @@ __device__ inline void split64(double x, int n, bool conductor, int &c, double &
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(256) k_push_fp64(Geom g, FieldPtrs<double> f, double *J0, double *J1, double *J2,
+__global__ void __launch_bounds__(256, 2) k_push_fp64(Geom g, FieldPtrs<double> f, double *J0, double *J1, double *J2,
                                                    Species64 sp, long long n, double h, double alpha, double dt,
                                                    int mode, double m_over_me, double *kin_acc, int *err) {
     GlobalSink64 sink;
