@@ -78,7 +78,41 @@ __device__ __forceinline__ void deposit_segment(const R d[3], const R D[3], R al
         w0[a] = R(1) - w1[a];
     }
     const R ax = -alpha * D[0], ay = -alpha * D[1], az = -alpha * D[2];
-    if (NDIM == 3) {
+    if constexpr (std::is_same<R, float>::value) {
+        // FP32: the same values by paired multiply-adds (two lanes per instruction,
+        // each lane rounded exactly as the scalar fused form below)
+        const float2 X = make_float2(w0[0], w1[0]), Y = make_float2(w0[1], w1[1]);
+        float2 t;
+        if (NDIM == 3) {
+            const float cyz = D[1] * D[2] * (1.f / 12.f), czx = D[2] * D[0] * (1.f / 12.f),
+                        cxy = D[0] * D[1] * (1.f / 12.f);
+            const float2 axx = make_float2(ax, ax), ayy = make_float2(ay, ay);
+            t = __fmul2_rn(axx, __ffma2_rn(Y, make_float2(w0[2], w0[2]), make_float2(cyz, -cyz)));
+            sink(0, 0, 0, 0, t.x); sink(0, 0, 1, 0, t.y);
+            t = __fmul2_rn(axx, __ffma2_rn(Y, make_float2(w1[2], w1[2]), make_float2(-cyz, cyz)));
+            sink(0, 0, 0, 1, t.x); sink(0, 0, 1, 1, t.y);
+            t = __fmul2_rn(ayy, __ffma2_rn(X, make_float2(w0[2], w0[2]), make_float2(czx, -czx)));
+            sink(1, 0, 0, 0, t.x); sink(1, 1, 0, 0, t.y);
+            t = __fmul2_rn(ayy, __ffma2_rn(X, make_float2(w1[2], w1[2]), make_float2(-czx, czx)));
+            sink(1, 0, 0, 1, t.x); sink(1, 1, 0, 1, t.y);
+            const float2 azz = make_float2(az, az);
+            t = __fmul2_rn(azz, __ffma2_rn(X, make_float2(w0[1], w0[1]), make_float2(cxy, -cxy)));
+            sink(2, 0, 0, 0, t.x); sink(2, 1, 0, 0, t.y);
+            t = __fmul2_rn(azz, __ffma2_rn(X, make_float2(w1[1], w1[1]), make_float2(-cxy, cxy)));
+            sink(2, 0, 1, 0, t.x); sink(2, 1, 1, 0, t.y);
+        } else {
+            const float cxy = D[0] * D[1] * (1.f / 12.f);
+            t = __fmul2_rn(make_float2(ax, ax), Y);
+            sink(0, 0, 0, 0, t.x); sink(0, 0, 1, 0, t.y);
+            t = __fmul2_rn(make_float2(ay, ay), X);
+            sink(1, 0, 0, 0, t.x); sink(1, 1, 0, 0, t.y);
+            const float2 azz = make_float2(az, az);
+            t = __fmul2_rn(azz, __ffma2_rn(X, make_float2(w0[1], w0[1]), make_float2(cxy, -cxy)));
+            sink(2, 0, 0, 0, t.x); sink(2, 1, 0, 0, t.y);
+            t = __fmul2_rn(azz, __ffma2_rn(X, make_float2(w1[1], w1[1]), make_float2(-cxy, cxy)));
+            sink(2, 0, 1, 0, t.x); sink(2, 1, 1, 0, t.y);
+        }
+    } else if (NDIM == 3) {
         const R cyz = D[1] * D[2] * R(1.0 / 12.0), czx = D[2] * D[0] * R(1.0 / 12.0),
                 cxy = D[0] * D[1] * R(1.0 / 12.0);
         // x faces (i+1/2, j+p, k+q)

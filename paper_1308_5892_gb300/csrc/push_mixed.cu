@@ -61,8 +61,10 @@ namespace {
 constexpr float kFx26 = 67108864.0f;   // 2^26: fixed-point scale of one flux
 constexpr unsigned kFull = 0xffffffffu;
 
-// The fixed-point value of one flux (see the header comment).
-__device__ __forceinline__ int fx(float v) { return __float2int_rn(v * kFx26); }
+// The fixed-point value of one flux (see the header comment).  The deposit's
+// prefactor carries the scale (alpha 2^26, a power of two, so every product is
+// the flux times 2^26 exactly), and v26 only needs rounding here.
+__device__ __forceinline__ int fx(float v26) { return __float2int_rn(v26); }
 
 // Global current sink for particles outside the staged box: the same
 // fixed-point value in units 2^-36, added as one int64 at the interior-wrapped
@@ -82,13 +84,13 @@ struct GlobalSinkFx {
 template <int NDIM>
 __device__ __noinline__ void deposit_global(const Geom &g, unsigned long long *J0, unsigned long long *J1,
                                             unsigned long long *J2, int ci, int cj, int ck, const float d[3],
-                                            const int s[3], const float d1[3], float dz, float sgn) {
+                                            const int s[3], const float d1[3], float dz, float alpha26) {
     GlobalSinkFx gs;
     gs.g = &g;
     gs.J[0] = J0; gs.J[1] = J1; gs.J[2] = J2;
     gs.ci = ci; gs.cj = cj; gs.ck = ck;
     PieceDeposit<NDIM, float, GlobalSinkFx> pd(gs);
-    deposit_path<NDIM, float>(d, s, d1, dz, sgn, pd);
+    deposit_path<NDIM, float>(d, s, d1, dz, alpha26, pd);
 }
 
 // Slow path of a particle reflected by a conducting wall in x (App. A.4):
@@ -97,7 +99,7 @@ __device__ __noinline__ void deposit_global(const Geom &g, unsigned long long *J
 template <int NDIM>
 __device__ __noinline__ void deposit_reflect(const Geom &g, unsigned long long *J0, unsigned long long *J1,
                                              unsigned long long *J2, int ci, int cj, int ck, const float d0[3],
-                                             const float D[3], int side, float sgn) {
+                                             const float D[3], int side, float alpha26) {
     const float wall = side < 0 ? 0.f : 1.f;           // in the x coordinates of cell ci
     const float t = (wall - d0[0]) / D[0];             // parameter of the wall hit, in [0, 1]
     const float L1[3] = {wall - d0[0], D[1] * t, D[2] * t};
@@ -120,7 +122,7 @@ __device__ __noinline__ void deposit_reflect(const Geom &g, unsigned long long *
             s[a] = (int)sa;
             d1[a] = da;
         }
-        deposit_global<NDIM>(g, J0, J1, J2, c[0], c[1], c[2], st, s, d1, L[2], sgn);
+        deposit_global<NDIM>(g, J0, J1, J2, c[0], c[1], c[2], st, s, d1, L[2], alpha26);
         // the second leg starts where the first ended
         st[0] = wall;
         for (int a = 1; a < NDIM; ++a) { c[a] += s[a]; st[a] = d1[a]; }
@@ -130,7 +132,9 @@ __device__ __noinline__ void deposit_reflect(const Geom &g, unsigned long long *
 template <int NDIM>
 __device__ __forceinline__ void gather_nodes(const float4 *nA, const float2 *nB, int q0, int sx, int sxy,
                                              const float d[3], float E[3], float B[3]) {
-    E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = 0.f;
+    // paired FP32 multiply-adds (two lanes of one instruction, each rounded as a
+    // single fused multiply-add): E_x E_y, E_z B_x and B_y B_z
+    float2 e01 = make_float2(0.f, 0.f), e2b0 = e01, b12 = e01;
 #pragma unroll
     for (int xi = 0; xi < (NDIM == 3 ? 2 : 1); ++xi)
 #pragma unroll
@@ -142,9 +146,13 @@ __device__ __forceinline__ void gather_nodes(const float4 *nA, const float2 *nB,
                 const int q = q0 + eps + eta * sx + xi * sxy;
                 const float4 a = nA[q];
                 const float2 b = nB[q];
-                E[0] += w * a.x; E[1] += w * a.y; E[2] += w * a.z;
-                B[0] += w * a.w; B[1] += w * b.x; B[2] += w * b.y;
+                const float2 ww = make_float2(w, w);
+                e01 = __ffma2_rn(ww, make_float2(a.x, a.y), e01);
+                e2b0 = __ffma2_rn(ww, make_float2(a.z, a.w), e2b0);
+                b12 = __ffma2_rn(ww, b, b12);
             }
+    E[0] = e01.x; E[1] = e01.y; E[2] = e2b0.x;
+    B[0] = e2b0.y; B[1] = b12.x; B[2] = b12.y;
 }
 
 template <int NDIM>
@@ -384,13 +392,13 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
 // Deposit the queued piece at ring position idx with shared-memory atomics.
 template <int NDIM>
 __device__ __forceinline__ void drain_one(const int *q_base, const float *q_d, const float *q_D, int idx,
-                                          const TileCtx &tc, float sgn) {
+                                          const TileCtx &tc, float alpha26) {
     const float d[3] = {q_d[idx], q_d[kQueue + idx], NDIM == 3 ? q_d[2 * kQueue + idx] : 0.f};
     const float D[3] = {q_D[idx], q_D[kQueue + idx], q_D[2 * kQueue + idx]};
     SmemSinkFx sd;
     sd.hi = tc.Jhi; sd.lo = tc.Jlo; sd.sx = tc.sx; sd.sxy = tc.sxy; sd.nodes = tc.nodes;
     sd.base = q_base[idx];
-    deposit_segment<NDIM, float>(d, D, sgn, sd);
+    deposit_segment<NDIM, float>(d, D, alpha26, sd);
 }
 
 // All species of one tile of one run (the body of both launch forms below).
@@ -494,7 +502,7 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
     int qhead = 0, qcount = 0;   // warp-uniform state of the piece ring
     for (int sp = 0; sp < a.nspecies; ++sp) {
         const SpeciesMixed &P = a.sp[sp];
-        const float h = a.h[sp], sgn = a.sgn[sp];
+        const float h = a.h[sp], alpha26 = a.sgn[sp] * kFx26;   // deposit prefactor in fixed-point units
         const int pbeg = a.tile_start[sp][tile], pend = a.tile_start[sp][tile + 1];
         const int nt = pend - pbeg;
         const int nblk = nt >> 10;                       // full 1024-blocks, stored transposed
@@ -519,7 +527,7 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
         auto drain_queue = [&]() {
             if (qcount > 0) {
                 __syncwarp();
-                if (lane < qcount) drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, sgn);
+                if (lane < qcount) drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, alpha26);
                 __syncwarp();
                 qhead = (qhead + qcount) & (kQueue - 1);
                 qcount = 0;
@@ -601,12 +609,12 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                         int cc[3];
                         float pd[3], pD[3];
                         ps.piece(0, cc, pd, pD);
-                        deposit_segment<NDIM, float>(pd, pD, sgn, acc);
+                        deposit_segment<NDIM, float>(pd, pD, alpha26, acc);
                         nc = ps.ncross;
                     } else if (!WALLS || side == 0) {
-                        deposit_global<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, s, d, D[2], sgn);
+                        deposit_global<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, s, d, D[2], alpha26);
                     } else {
-                        deposit_reflect<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, D, side, sgn);
+                        deposit_reflect<NDIM>(g, a.J[0], a.J[1], a.J[2], ci, cj, ck, d0, D, side, alpha26);
                     }
                 }
                 // pieces after a crossing: append to the warp's ring, drain 32 at a time
@@ -631,7 +639,7 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
                     qcount += __popc(m);
                     if (qcount >= 32) {
                         __syncwarp();
-                        drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, sgn);
+                        drain_one<NDIM>(q_base, q_d, q_D, (qhead + lane) & (kQueue - 1), tc, alpha26);
                         __syncwarp();
                         qhead = (qhead + 32) & (kQueue - 1);
                         qcount -= 32;
