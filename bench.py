@@ -392,9 +392,10 @@ def _ensemble_leg(pic, torch, args, seed, barrier, dist):
         return e0.elapsed_time(e1)
 
     ms = max_over_ranks(window(0), dist, "cuda")
+    launches = ctx.counters()["launches_per_step"]
+    # per-kernel events need the phase launches: the step walker runs every phase in one launch
     window(pic.PIC_FLAG_TIMING)
     push_ms, push_n = ctx.kernel_time(pic.PIC_KERNEL_PUSH)
-    launches = ctx.counters()["launches_per_step"]
     ctx.close()
     del ctx
     torch.cuda.empty_cache()
@@ -406,7 +407,8 @@ def _ensemble_leg(pic, torch, args, seed, barrier, dist):
             "value": job_value(npart, steps, ms, world), "unit": "particle-steps/ns", "ms_per_step": ms / steps,
             "tuning": tuned, "launches_per_step": launches,
             "roofline": None if ach is None else {
-                "bound": "hbm", "kernel": "k_push_mixed_multi (all runs, one persistent launch)", "achieved": ach,
+                "bound": "hbm", "kernel": "k_push_mixed_multi (all runs, one persistent launch; timed in the "
+                "phase-launch form of the step, the value window runs the step walker)", "achieved": ach,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
                 "push_ms_per_step": push_step, "bytes_per_particle_step": 48.0}}
 

@@ -55,6 +55,14 @@ typedef enum { PIC_MJ_EXACT = 0, PIC_MJ_MLP = 1, PIC_MJ_NAIVE_BOOST = 2 } pic_mj
 #define PIC_FLAG_ASYNC 1u      /* pic_step returns without synchronising */
 #define PIC_FLAG_NO_GRAPH 2u   /* pic_step launches kernels directly instead of replaying a CUDA graph */
 #define PIC_FLAG_TIMING 4u     /* record CUDA events around each kernel class (see pic_kernel_time) */
+/* Ensembles of PIC_MIXED runs: one batched launch per phase of the step
+ * instead of the persistent step walker (see pic_step). */
+#define PIC_FLAG_PHASE_LAUNCHES 8u
+/* Test hook of the step walker's bounded waits: the push phase of run 0 waits
+ * for one item more than exist, so its wait runs out after 20 ms, the launch
+ * ends and pic_step reports PIC_ETIMEOUT; the state of that step is undefined.
+ * Nothing faults: every wait is bounded and the kernel returns. */
+#define PIC_FLAG_INJECT_STALL 16u
 
 /* Kernel classes timed under PIC_FLAG_TIMING. */
 typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_FIELD = 1, PIC_KERNEL_SORT = 2, PIC_KERNEL_SMOOTH = 3 } pic_kernel_class;
@@ -247,7 +255,12 @@ pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double p
  * does not run the steps) and launched on the context stream; later periods
  * replay it while the state it was captured from is unchanged, so results
  * are bitwise those of direct launches.  A failed capture falls back to
- * direct launches. */
+ * direct launches.
+ * Ensembles (nruns > 1, PIC_MIXED): unless PIC_FLAG_PHASE_LAUNCHES or
+ * PIC_FLAG_TIMING, each step is one persistent launch (the step walker: a work
+ * queue of (phase, run, tile or cell chunk) items with per-run dependencies and
+ * bounded waits), plus the batched sort launches on the steps that sort; the
+ * fields and particles are bitwise those of the phase launches. */
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
 /* Wait for queued work and report the device-side error flag. */

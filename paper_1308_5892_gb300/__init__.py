@@ -20,7 +20,7 @@ PIC_FP64, PIC_MIXED = 0, 1
 PIC_BC_PERIODIC, PIC_BC_CONDUCTOR = 0, 1
 PIC_PROFILE_UNIFORM, PIC_PROFILE_HARRIS = 0, 1
 PIC_MJ_EXACT, PIC_MJ_MLP, PIC_MJ_NAIVE_BOOST = 0, 1, 2
-PIC_FLAG_ASYNC, PIC_FLAG_NO_GRAPH, PIC_FLAG_TIMING = 1, 2, 4
+PIC_FLAG_ASYNC, PIC_FLAG_NO_GRAPH, PIC_FLAG_TIMING, PIC_FLAG_PHASE_LAUNCHES, PIC_FLAG_INJECT_STALL = 1, 2, 4, 8, 16
 PIC_KERNEL_PUSH, PIC_KERNEL_FIELD, PIC_KERNEL_SORT, PIC_KERNEL_SMOOTH = 0, 1, 2, 3
 MAX_SPECIES = 4
 

@@ -103,6 +103,10 @@ struct pic_ctx {
     MixedStepArgs *multi_args = nullptr;
     FieldRunF *multi_fe = nullptr, *multi_fp = nullptr;
     int *multi_tiles = nullptr, *multi_blocks = nullptr, *multi_counter = nullptr;
+    int *walk_tab = nullptr, *walk_ctl = nullptr;   // step walker: queue tables; head, abort, done[nruns]
+    std::vector<int> h_walk;
+    int walk_fit[2][2] = {{-1, -1}, {-1, -1}};      // walk_fits() by (walls, count) for walk_fit_smem
+    size_t walk_fit_smem = 0;
     int multi_nblocks = 0;
     bool multi_tiles_dirty = false;
     std::vector<MixedStepArgs> h_args;
@@ -775,6 +779,20 @@ FieldRunF field_run(Run &r, bool energy, bool inc) {
     return fr;
 }
 
+// Ints of the step walker's queue tables: prefix [kWalkMaxPhases * nr + 1], base [nr * (kWalkMaxPhases + 1)].
+size_t walk_tab_ints(int nr) { return (size_t)kWalkMaxPhases * nr + 1 + (size_t)nr * (kWalkMaxPhases + 1); }
+
+// Can the step walker run with this push shared memory (cached per context)?
+bool walk_ok(pic_ctx *ctx, int ndim, bool walls, bool count, size_t smem) {
+    if (smem != ctx->walk_fit_smem) {
+        ctx->walk_fit[0][0] = ctx->walk_fit[0][1] = ctx->walk_fit[1][0] = ctx->walk_fit[1][1] = -1;
+        ctx->walk_fit_smem = smem;
+    }
+    int &f = ctx->walk_fit[walls ? 1 : 0][count ? 1 : 0];
+    if (f < 0) f = walk_fits(ndim, walls, count, smem) ? 1 : 0;
+    return f == 1;
+}
+
 // Host source of an argument-table upload: the table itself, or (slot >= 0,
 // while a graph is captured) its copy in the pinned region of that step, which
 // the captured copy node reads again at every replay.
@@ -786,8 +804,11 @@ const void *host_src(pic_ctx *ctx, int slot, size_t &off, const void *data, size
     return dst;
 }
 
-// One step of every run of a mixed ensemble: per-run sorts when due, then one
-// batched launch per field phase and one persistent push launch for all runs.
+// One step of every run of a mixed ensemble: per-run sorts when due (one
+// batched launch per sort phase), then the step walker (one persistent launch
+// for every phase of every run), or with PIC_FLAG_PHASE_LAUNCHES or
+// PIC_FLAG_TIMING one batched launch per field phase and one persistent push
+// launch for all runs.
 pic_status step_multi(pic_ctx *ctx, int slot) {
     size_t soff = 0;
     cudaStream_t s = ctx->stream;
@@ -857,6 +878,88 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
     CK(cudaMemcpyAsync(ctx->multi_fp, host_src(ctx, slot, soff, ctx->h_fp.data(), sizeof(FieldRunF) * nr),
                        sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
     const float dt = (float)ctx->runs[0].d.dt;
+    int max_smooth = 0;
+    for (auto &r : ctx->runs) max_smooth = std::max(max_smooth, r.smooth);
+    const int ndim = ctx->runs[0].d.ndim;
+    const bool walls = ctx->runs[0].g.bcx == 1;
+    const size_t push_smem = mixed_smem_bytes(ctx->runs[0].t, ndim);
+    const int nphase = 5 + (max_smooth > 0 ? 1 + max_smooth : 0);
+    if (!(ctx->flags & (PIC_FLAG_PHASE_LAUNCHES | PIC_FLAG_TIMING)) && nphase <= kWalkMaxPhases &&
+        walk_ok(ctx, ndim, walls, count, push_smem)) {
+        // the whole step in one persistent launch (walk.cu)
+        WalkArgs w{};
+        int np = 0;
+        w.kind[np++] = W_B_HALF_E;
+        w.kind[np++] = W_NODE;
+        w.kind[np++] = W_PUSH;
+        if (max_smooth > 0) {
+            w.kind[np++] = W_SMOOTH_FOLD;
+            for (int p = 0; p < max_smooth; ++p) {
+                w.pass[np] = p;
+                w.kind[np++] = W_SMOOTH_PASS;
+            }
+        }
+        w.kind[np++] = W_B_HALF;
+        w.kind[np++] = W_E_FX;
+        const int cpi = walk_cells_per_item(ndim);
+        auto items = [&](int ph, const Run &r) -> int {
+            const long long ncell = (long long)r.g.nx * r.g.ny * r.g.nz;
+            switch (w.kind[ph]) {
+            case W_PUSH: return r.t.ntiles;
+            case W_SMOOTH_FOLD: return r.smooth > 0 ? (int)((ncell + cpi - 1) / cpi) : 0;
+            case W_SMOOTH_PASS: return r.smooth > w.pass[ph] ? (int)((ncell + cpi - 1) / cpi) : 0;
+            default: return (int)((r.g.pcells + cpi - 1) / cpi);
+            }
+        };
+        int *prefix = ctx->h_walk.data(), *base = prefix + np * nr + 1;
+        int total = 0;
+        for (int ph = 0; ph < np; ++ph)
+            for (int i = 0; i < nr; ++i) {
+                prefix[ph * nr + i] = total;
+                total += items(ph, ctx->runs[i]);
+            }
+        prefix[np * nr] = total;
+        for (int i = 0; i < nr; ++i) {
+            base[i * (np + 1)] = 0;
+            for (int ph = 0; ph < np; ++ph) base[i * (np + 1) + ph + 1] = base[i * (np + 1) + ph] + items(ph, ctx->runs[i]);
+        }
+        // test hook: the push of run 0 waits for an item that does not exist
+        if (ctx->flags & PIC_FLAG_INJECT_STALL) base[2] += 1;
+        const size_t tab = sizeof(int) * ((size_t)np * nr + 1 + (size_t)nr * (np + 1));
+        CK(cudaMemcpyAsync(ctx->walk_tab, host_src(ctx, slot, soff, ctx->h_walk.data(), tab), tab,
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(ctx->walk_ctl, 0, sizeof(int) * (2 + nr), s));
+        w.push = ctx->multi_args;
+        w.fe = ctx->multi_fe;
+        w.fp = ctx->multi_fp;
+        w.prefix = ctx->walk_tab;
+        w.base = ctx->walk_tab + np * nr + 1;
+        w.head = ctx->walk_ctl;
+        w.abort = ctx->walk_ctl + 1;
+        w.done = ctx->walk_ctl + 2;
+        w.err = ctx->d_err;
+        w.nruns = nr;
+        w.nphase = np;
+        w.total = total;
+        w.cells_per_item = cpi;
+        w.h = 0.5f * dt;
+        w.dt = dt;
+        w.wait_ns = (ctx->flags & PIC_FLAG_INJECT_STALL) ? 20000000LL : 2000000000LL;
+        launch_walk(w, ndim, walls, count, push_smem, s);
+        CK(cudaGetLastError());
+        if (count)
+            for (auto &r : ctx->runs)
+                for (int q = 0; q < r.d.nspecies; ++q) r.sp[q].counted = true;
+        for (auto &r : ctx->runs) {
+            r.since_sort++;
+            r.jcur = 1 - r.jcur;
+            r.step++;
+            if (r.hist_n < r.hist_cap) r.hist_n++;
+        }
+        ctx->launch_total += launches + 1;
+        ctx->bytes_per_ps = ndim == 2 ? 48.0 : 56.0;
+        return PIC_OK;
+    }
     {
         KTimer t(ctx, PIC_KERNEL_FIELD);
         launch_fields_multi(FIELD_B_HALF, ctx->multi_fe, ctx->multi_blocks, ctx->multi_nblocks, nr, 0.5f * dt, dt, s);
@@ -871,8 +974,6 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
             for (auto &r : ctx->runs)
                 for (int q = 0; q < r.d.nspecies; ++q) r.sp[q].counted = true;
     }
-    int max_smooth = 0;
-    for (auto &r : ctx->runs) max_smooth = std::max(max_smooth, r.smooth);
     if (max_smooth > 0) {
         KTimer t(ctx, PIC_KERNEL_SMOOTH);
         launch_smooth_multi(0, 0, ctx->multi_fp, ctx->multi_blocks, ctx->multi_nblocks, nr, s);
@@ -1044,6 +1145,7 @@ bool graph_aligned(const pic_ctx *ctx) {
 std::vector<long long> graph_signature(const pic_ctx *ctx) {
     std::vector<long long> v;
     v.push_back((long long)(uintptr_t)ctx->stream);
+    v.push_back(ctx->flags & PIC_FLAG_PHASE_LAUNCHES);
     for (const auto &r : ctx->runs) {
         v.push_back(r.jcur);
         v.push_back(r.sort_interval);
@@ -1084,7 +1186,8 @@ pic_status capture_graph(pic_ctx *ctx) {
         const size_t a = 256;
         auto up = [a](size_t b) { return (b + a - 1) & ~(a - 1); };
         const size_t stride = up(sizeof(MixedStepArgs) * nr) + 2 * up(sizeof(FieldRunF) * nr) +
-                              maxsp * (up(sizeof(SortArgs) * nr) + up(sizeof(int) * 4 * (nr + 1)));
+                              maxsp * (up(sizeof(SortArgs) * nr) + up(sizeof(int) * 4 * (nr + 1))) +
+                              up(sizeof(int) * walk_tab_ints(nr));
         if (ctx->gstage_bytes < stride * P) {
             if (ctx->gstage) cudaFreeHost(ctx->gstage);
             ctx->gstage = nullptr;
@@ -1192,12 +1295,15 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
         ctx->multi_tiles = (int *)dev_alloc(ctx, sizeof(int) * (nruns + 1));
         ctx->multi_blocks = (int *)dev_alloc(ctx, sizeof(int) * (nruns + 1));
         ctx->multi_counter = (int *)dev_alloc(ctx, sizeof(int));
+        ctx->walk_tab = (int *)dev_alloc(ctx, sizeof(int) * walk_tab_ints(nruns));
+        ctx->walk_ctl = (int *)dev_alloc(ctx, sizeof(int) * (2 + nruns));
+        ctx->h_walk.resize(walk_tab_ints(nruns));
         ctx->sort_args_dev = (SortArgs *)dev_alloc(ctx, sizeof(SortArgs) * nruns);
         ctx->sort_prefix_dev = (int *)dev_alloc(ctx, sizeof(int) * 4 * (nruns + 1));
         ctx->h_sort.resize(nruns);
         ctx->h_sort_prefix.resize(4 * (nruns + 1));
         if (!ctx->multi_args || !ctx->multi_fe || !ctx->multi_fp || !ctx->multi_tiles || !ctx->multi_blocks ||
-            !ctx->multi_counter || !ctx->sort_args_dev || !ctx->sort_prefix_dev) {
+            !ctx->multi_counter || !ctx->sort_args_dev || !ctx->sort_prefix_dev || !ctx->walk_tab || !ctx->walk_ctl) {
             pic_destroy(ctx);
             return PIC_ENOMEM;
         }
@@ -1472,7 +1578,8 @@ pic_status pic_step(pic_ctx *ctx, int nsteps) {
     if (nsteps < 0) return fail(ctx, PIC_EINVAL, "nsteps must be >= 0");
     int n = 0;
     ctx->launch_total = 0;
-    const bool graphs = ctx->precision == PIC_MIXED && !(ctx->flags & (PIC_FLAG_NO_GRAPH | PIC_FLAG_TIMING));
+    const bool graphs = ctx->precision == PIC_MIXED &&
+                        !(ctx->flags & (PIC_FLAG_NO_GRAPH | PIC_FLAG_TIMING | PIC_FLAG_INJECT_STALL));
     while (n < nsteps) {
         if (graphs && graph_aligned(ctx) && nsteps - n >= graph_period_of(ctx)) {
             const int P = graph_period_of(ctx);
@@ -1506,7 +1613,8 @@ pic_status pic_step(pic_ctx *ctx, int nsteps) {
 
 pic_status pic_set_flags(pic_ctx *ctx, uint32_t flags) {
     if (!ctx) return PIC_EINVAL;
-    if (flags & ~(PIC_FLAG_ASYNC | PIC_FLAG_NO_GRAPH | PIC_FLAG_TIMING)) return fail(ctx, PIC_EINVAL, "unknown flag bits");
+    if (flags & ~(PIC_FLAG_ASYNC | PIC_FLAG_NO_GRAPH | PIC_FLAG_TIMING | PIC_FLAG_PHASE_LAUNCHES | PIC_FLAG_INJECT_STALL))
+        return fail(ctx, PIC_EINVAL, "unknown flag bits");
     ctx->flags = flags;
     return PIC_OK;
 }

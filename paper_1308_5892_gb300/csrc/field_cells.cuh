@@ -32,7 +32,7 @@ __device__ inline void padded_coords(const Geom &g, long long p, int &pi, int &p
 }
 
 template <typename R>
-__device__ inline R ld(const R *a, long long i) { return __ldg(a + i); }
+__device__ inline R ld(const R *a, long long i) { return ldro(a + i); }
 
 // Block-wide FP64 sum of NV values, one atomicAdd per value per block.
 template <int NV>
@@ -217,9 +217,9 @@ __device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R
         const F2 curl_x = curl_pair(bz, ld(f.b[2], g.widx(i, j - 1, k)), by, ld(f.b[1], g.widx(i, j, k - 1)));
         const F2 curl_y = curl_pair(bx, ld(f.b[0], g.widx(i, j, k - 1)), bz, ld(f.b[2], g.widx(i - 1, j, k)));
         const F2 curl_z = curl_pair(by, ld(f.b[1], g.widx(i - 1, j, k)), bx, ld(f.b[0], g.widx(i, j - 1, k)));
-        F2 ex = e_pair_update(f, 0, p, dt, curl_x, sc, (long long)__ldg(Js + q));
-        F2 ey = e_pair_update(f, 1, p, dt, curl_y, sc, (long long)__ldg(Js + ncell + q));
-        F2 ez = e_pair_update(f, 2, p, dt, curl_z, sc, (long long)__ldg(Js + 2 * ncell + q));
+        F2 ex = e_pair_update(f, 0, p, dt, curl_x, sc, (long long)ldro(Js + q));
+        F2 ey = e_pair_update(f, 1, p, dt, curl_y, sc, (long long)ldro(Js + ncell + q));
+        F2 ez = e_pair_update(f, 2, p, dt, curl_z, sc, (long long)ldro(Js + 2 * ncell + q));
         if (g.bcx == 1 && i == 0) { ey = F2{0.f, 0.f}; ez = F2{0.f, 0.f}; }
         e_pair_store(f, 0, p, ex);
         e_pair_store(f, 1, p, ey);
@@ -228,9 +228,9 @@ __device__ __forceinline__ void e_smoothed_cell(const Geom &g, const FieldPtrs<R
         const R curl_x = (bz - ld(f.b[2], g.widx(i, j - 1, k))) - (by - ld(f.b[1], g.widx(i, j, k - 1)));
         const R curl_y = (bx - ld(f.b[0], g.widx(i, j, k - 1))) - (bz - ld(f.b[2], g.widx(i - 1, j, k)));
         const R curl_z = (by - ld(f.b[1], g.widx(i - 1, j, k))) - (bx - ld(f.b[0], g.widx(i, j - 1, k)));
-        const R jx = (R)(scale * (double)__ldg(Js + q));
-        const R jy = (R)(scale * (double)__ldg(Js + ncell + q));
-        const R jz = (R)(scale * (double)__ldg(Js + 2 * ncell + q));
+        const R jx = (R)(scale * (double)ldro(Js + q));
+        const R jy = (R)(scale * (double)ldro(Js + ncell + q));
+        const R jz = (R)(scale * (double)ldro(Js + 2 * ncell + q));
         R ex = f.e[0][p] + dt * curl_x + jx;
         R ey = f.e[1][p] + dt * curl_y + jy;
         R ez = f.e[2][p] + dt * curl_z + jz;
@@ -251,7 +251,7 @@ __device__ inline float sval(const Geom &g, const float *a, bool xstag, int i, i
         if (xstag) { if (i < 0 || i > g.nx - 1) return 0.f; }
         else { if (i <= 0 || i >= g.nx) return 0.f; }
     }
-    return __ldg(a + g.widx(i, j, k));
+    return ldro(a + g.widx(i, j, k));
 }
 
 // Node-averaged fields (App. A.3.3) at every padded node: e over its two edge

@@ -55,6 +55,20 @@ struct FastDiv {
     }
 };
 
+// Load of an array that the kernel does not write.  A translation unit that
+// defines PIC_COHERENT_LOADS before including this header (the persistent
+// ensemble step, whose CTAs read arrays that other CTAs of the same launch
+// wrote) gets plain loads; the others use the read-only data path.  Internal
+// linkage: each translation unit keeps its own form.
+template <typename T>
+static __device__ __forceinline__ T ldro(const T *p) {
+#ifdef PIC_COHERENT_LOADS
+    return *p;
+#else
+    return __ldg(p);
+#endif
+}
+
 // Periodic wrap into [0, n): arguments within one period of the range (all
 // the stencils and ghosts here) take two selects, others the modulo.
 __host__ __device__ inline int wrap_index(int i, int n) {
@@ -271,6 +285,32 @@ void launch_smooth_multi(int phase, int pass, const FieldRunF *runs_dev, const i
 void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB, SpeciesMixed sp, long long n,
                             float h, float dt, cudaStream_t s);
 size_t mixed_smem_bytes(const TileGeom &t, int ndim);
+
+// walk.cu: the persistent step of a mixed ensemble (one launch per step).
+// Phases of one step, in order; every item of phase ph of run r waits until all
+// items of run r in phases before ph are done.
+enum WalkPhase { W_B_HALF_E = 0, W_NODE, W_PUSH, W_SMOOTH_FOLD, W_SMOOTH_PASS, W_B_HALF, W_E_FX };
+constexpr int kWalkMaxPhases = 16;
+struct WalkArgs {
+    const MixedStepArgs *push;     // per run
+    const FieldRunF *fe, *fp;      // per run: first b half advance (records the energies); other field phases
+    const int *prefix;             // [nphase * nruns + 1]: first queue item of (phase, run), phase-major
+    const int *base;               // [nruns * (nphase + 1)]: items of run r in the phases before each phase
+    int *head;                     // queue counter (zero before the launch)
+    int *abort;                    // set when a wait runs out (zero before the launch)
+    int *done;                     // [nruns] items of each run done (zero before the launch)
+    int *err;
+    int nruns, nphase, total;
+    int cells_per_item;            // cells of one field or smoothing item
+    int kind[kWalkMaxPhases];      // WalkPhase of each phase
+    int pass[kWalkMaxPhases];      // smoothing pass of a W_SMOOTH_PASS phase
+    float h, dt;                   // h = dt/2 (half advances of b)
+    long long wait_ns;             // bound of one wait (device global timer, ns)
+};
+int walk_cells_per_item(int ndim);
+// Can the walker run a step with this push shared memory on this device?
+bool walk_fits(int ndim, bool walls, bool count, size_t push_smem);
+void launch_walk(const WalkArgs &w, int ndim, bool walls, bool count, size_t push_smem, cudaStream_t s);
 // dynamic shared memory a push CTA may use (227 KB per block, less the kernels' static shared memory)
 constexpr size_t kMaxPushSmem = 224 * 1024;
 

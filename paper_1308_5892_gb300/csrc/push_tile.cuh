@@ -172,8 +172,8 @@ __device__ __noinline__ void gather_global(const Geom &g, const float4 *nA, cons
                 // masked averages of the high wall, which differ from node 0's
                 const long long q = g.bcx == 1 ? g.pidx(ci + eps, g.wy(cj + eta), g.wz(ck + xi))
                                                : g.widx(ci + eps, cj + eta, ck + xi);
-                const float4 a = __ldg(nA + q);
-                const float2 b = __ldg(nB + q);
+                const float4 a = ldro(nA + q);
+                const float2 b = ldro(nB + q);
                 E[0] += w * a.x; E[1] += w * a.y; E[2] += w * a.z;
                 B[0] += w * a.w; B[1] += w * b.x; B[2] += w * b.y;
             }
@@ -339,14 +339,16 @@ __device__ __forceinline__ void push_one(const MixedStepArgs &a, const TileCtx &
     float E[3], B[3];
     if (fast) gather_nodes<NDIM>(tc.nA, tc.nB, q0, tc.sx, tc.sxy, d, E, B);
     else gather_global<NDIM>(g, a.nfA, a.nfB, ci, cj, ck, d, E, B);
-    const float u2_0 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    // explicit roundings (nothing left to contract), so that every kernel that
+    // inlines this body computes the same bits
+    const float u2_0 = __fmaf_rn(u[2], u[2], __fmaf_rn(u[1], u[1], __fmul_rn(u[0], u[0])));
     const float dt = a.dt;
     boris<float>(u, E, B, h, dt);
-    const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const float inv_gam = rsqrtf(1.f + u2);
+    const float u2 = __fmaf_rn(u[2], u[2], __fmaf_rn(u[1], u[1], __fmul_rn(u[0], u[0])));
+    const float inv_gam = rsqrtf(__fadd_rn(1.f, u2));
     // gamma - 1 = u^2 / (1 + gamma), free of cancellation
-    kin0 += __fdividef(u2_0, 1.f + (1.f + u2_0) * rsqrtf(1.f + u2_0));
-    kin1 += __fdividef(u2, 1.f + (1.f + u2) * inv_gam);
+    kin0 = __fadd_rn(kin0, __fdividef(u2_0, __fmaf_rn(__fadd_rn(1.f, u2_0), rsqrtf(__fadd_rn(1.f, u2_0)), 1.f)));
+    kin1 = __fadd_rn(kin1, __fdividef(u2, __fmaf_rn(__fadd_rn(1.f, u2), inv_gam, 1.f)));
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         D[ax] = dt * u[ax] * inv_gam;
@@ -454,8 +456,8 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
             float2 vb = make_float2(0.f, 0.f);
             if (gx < g.px && gy < g.py && gz < g.pz) {
                 const long long p = ((long long)gz * g.py + gy) * g.px + gx;
-                va = __ldg(a.nfA + p);
-                vb = __ldg(a.nfB + p);
+                va = ldro(a.nfA + p);
+                vb = ldro(a.nfB + p);
             }
             nA[q] = va;
             nB[q] = vb;

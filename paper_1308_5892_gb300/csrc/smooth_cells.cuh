@@ -55,14 +55,14 @@ template <typename JT>
 struct PaddedPlane {
     const JT *a;
     __device__ inline typename SmoothValue<JT>::type at(const Geom &g, int i, int j, int k) const {
-        return value_of(__ldg(a + g.pidx(i, j, k)));
+        return value_of(ldro(a + g.pidx(i, j, k)));
     }
 };
 template <typename T>
 struct CompactPlane {
     const T *a;
     __device__ inline T at(const Geom &g, int i, int j, int k) const {
-        return __ldg(a + ((long long)k * g.ny + j) * g.nx + i);
+        return ldro(a + ((long long)k * g.ny + j) * g.nx + i);
     }
 };
 

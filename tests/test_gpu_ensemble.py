@@ -1,11 +1,13 @@
-"""Batched ensemble (many independent runs in one context, one persistent push
-launch per step) and the autotuner.  Both are checked for exactness: an
+"""Batched ensemble (many independent runs in one context, one persistent
+launch per step: the step walker) and the autotuner.  Both are checked for exactness: an
 ensemble member must be bitwise identical to the same run advanced alone, and
 a run advanced under the autotuner's trials must be bitwise identical to the
 same run advanced with the default tuning (each particle's arithmetic is the
 same and the current is an exact fixed-point sum).  Each member of an
 ensemble is also compared with the FP64 oracle stepped from its own uploaded
 (FP32-rounded) state, at the mixed path's parity bars."""
+import time
+
 import numpy as np
 import pytest
 
@@ -145,3 +147,82 @@ def test_ensemble_members_match_oracle(walls):
             assert step == 12
             _member_vs_oracle(f, p, st, 2e-4, 2e-4, 2e-4, (walls, r, 12))
 
+
+
+def _random_ensemble(runs, bc, seed0):
+    descs, states = [], []
+    for r, (nx, ny, ppc, amp, sm) in enumerate(runs):
+        arr = synth.random_state_arrays(seed0 + r, 2, nx, ny, 1, ppc=ppc, spread=0.6, amp_e=amp, amp_b=amp,
+                                        colocate=False)
+        n = arr["species"][0]["pos"].shape[1]
+        descs.append(pic.run_desc(2, nx, ny, 1, 2.0, 8.0, 0.5, [(-1.0, 1.0, n), (1.0, 1.0, n)], bc=bc,
+                                  smooth_passes=sm))
+        states.append((np.concatenate([arr["e"], arr["b"]]), [np.concatenate([sp["pos"], sp["u"]])
+                                                              for sp in arr["species"]]))
+    return descs, states
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_step_walker_equals_phase_launches_bitwise(walls):
+    """The step walker (every phase of every run in one persistent launch, with
+    per-run dependencies) and one batched launch per phase advance the same
+    uneven ensemble to bitwise the same fields and particles: 14 steps with
+    re-sorts every 4 steps, graph replay on, members with 1 and 2 smoothing
+    passes in the periodic case, conducting x-walls in the other.  The walker
+    queues one kernel launch per step where the phase launches queue five or
+    more; the energy histories agree to 1e-6 (the kinetic energy is summed in
+    FP32 per block of particles, whose order inside a cell the sort's atomics
+    set)."""
+    runs = WALL_RUNS if walls else ORACLE_RUNS
+    descs, states = _random_ensemble(runs, (1, 0, 0) if walls else (0, 0, 0), 700)
+    out = []
+    for flags in (0, pic.PIC_FLAG_PHASE_LAUNCHES):
+        with pic.Context(descs, precision=pic.PIC_MIXED, sort_interval=4, flags=flags) as ens:
+            for r, (fields, parts) in enumerate(states):
+                ens.set_state(r, fields, parts)
+            ens.step(14)
+            launches = ens.counters()["launches_per_step"]
+            out.append(([ens.get_state(r) for r in range(len(runs))],
+                        [ens.energy_history(r) for r in range(len(runs))], launches))
+    (walk, hw, lw), (phase, hp, lp) = out
+    for r in range(len(runs)):
+        assert walk[r][2] == phase[r][2] == 14
+        assert np.array_equal(walk[r][0], phase[r][0]), r
+        for s in range(2):
+            assert np.array_equal(walk[r][1][s], phase[r][1][s]), (r, s)
+        # the order of the particles inside a cell (set by the sort's atomics) changes
+        # the FP32 partial sums of the kinetic energy at the 1e-8 level
+        np.testing.assert_allclose(hw[r], hp[r], rtol=1e-6, atol=0)
+    assert lw < lp, (lw, lp)
+
+
+def test_step_walker_bounded_wait_reports_timeout():
+    """A dependency that never completes (PIC_FLAG_INJECT_STALL: the push of run
+    0 waits for one item more than exist) makes the walker's bounded wait run
+    out after 20 ms: pic_step returns PIC_ETIMEOUT within seconds, nothing
+    faults, and the context stays usable: the states set again afterwards step
+    to bitwise the result of a fresh context."""
+    descs, states = _random_ensemble(ORACLE_RUNS[:3], (0, 0, 0), 900)
+    with pic.Context(descs, precision=pic.PIC_MIXED, sort_interval=4,
+                     flags=pic.PIC_FLAG_INJECT_STALL | pic.PIC_FLAG_NO_GRAPH) as ens:
+        for r, (fields, parts) in enumerate(states):
+            ens.set_state(r, fields, parts)
+        t0 = time.time()
+        with pytest.raises(pic.PicError) as ei:
+            ens.step(1)
+        assert ei.value.status == pic.PIC_ETIMEOUT
+        assert time.time() - t0 < 10.0
+        ens.set_flags(0)
+        for r, (fields, parts) in enumerate(states):
+            ens.set_state(r, fields, parts)
+        ens.step(5)
+        got = [ens.get_state(r) for r in range(len(descs))]
+    with pic.Context(descs, precision=pic.PIC_MIXED, sort_interval=4) as ref:
+        for r, (fields, parts) in enumerate(states):
+            ref.set_state(r, fields, parts)
+        ref.step(5)
+        want = [ref.get_state(r) for r in range(len(descs))]
+    for r in range(len(descs)):
+        assert np.array_equal(got[r][0], want[r][0]), r
+        for s in range(2):
+            assert np.array_equal(got[r][1][s], want[r][1][s]), (r, s)
