@@ -105,6 +105,8 @@ struct pic_ctx {
     int *multi_tiles = nullptr, *multi_blocks = nullptr, *multi_counter = nullptr;
     int *walk_tab = nullptr, *walk_ctl = nullptr;   // step walker: queue tables; head, abort, done[nruns]
     std::vector<int> h_walk;
+    SortArgs *walk_sort_dev = nullptr;              // step walker: sort arguments, [nruns * 4]
+    std::vector<SortArgs> h_walk_sort;
     int walk_fit[2][2] = {{-1, -1}, {-1, -1}};      // walk_fits() by (walls, count) for walk_fit_smem
     size_t walk_fit_smem = 0;
     int multi_nblocks = 0;
@@ -779,8 +781,9 @@ FieldRunF field_run(Run &r, bool energy, bool inc) {
     return fr;
 }
 
-// Ints of the step walker's queue tables: prefix [kWalkMaxPhases * nr + 1], base [nr * (kWalkMaxPhases + 1)].
-size_t walk_tab_ints(int nr) { return (size_t)kWalkMaxPhases * nr + 1 + (size_t)nr * (kWalkMaxPhases + 1); }
+// Ints of the step walker's queue tables: prefix [kWalkMaxPhases * nr + 1], base [nr * (kWalkMaxPhases + 1)],
+// order [nr].
+size_t walk_tab_ints(int nr) { return (size_t)kWalkMaxPhases * nr + 1 + (size_t)nr * (kWalkMaxPhases + 2); }
 
 // Can the step walker run with this push shared memory (cached per context)?
 bool walk_ok(pic_ctx *ctx, int ndim, bool walls, bool count, size_t smem) {
@@ -814,17 +817,47 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
     cudaStream_t s = ctx->stream;
     const int nr = (int)ctx->runs.size();
     int launches = 0;
-    // runs whose sort is due: species q of all of them is sorted by one launch per phase
+    // runs whose sort is due
     std::vector<int> due;
+    std::vector<char> is_due(nr, 0);
     int maxsp = 0;
     for (int i = 0; i < nr; ++i) {
         Run &r = ctx->runs[i];
         if (!r.sorted || r.since_sort >= r.sort_interval) {
             due.push_back(i);
+            is_due[i] = 1;
             maxsp = std::max(maxsp, r.d.nspecies);
         }
     }
-    if (!due.empty()) {
+    // when the next step sorts every run, this step's push counts their key histograms
+    bool count = true;
+    for (int i = 0; i < nr; ++i) {
+        const Run &r = ctx->runs[i];
+        const int since = is_due[i] ? 0 : r.since_sort;
+        if (!(since + 1 >= r.sort_interval && r.t.lg[0] >= 0)) count = false;
+    }
+    const float dt = (float)ctx->runs[0].d.dt;
+    int max_smooth = 0;
+    for (auto &r : ctx->runs) max_smooth = std::max(max_smooth, r.smooth);
+    const int ndim = ctx->runs[0].d.ndim;
+    const bool walls = ctx->runs[0].g.bcx == 1;
+    const size_t push_smem = mixed_smem_bytes(ctx->runs[0].t, ndim);
+    const int nphase = (due.empty() ? 0 : 8 * maxsp) + 5 + (max_smooth > 0 ? 1 + max_smooth : 0);
+    const bool walk = !(ctx->flags & (PIC_FLAG_PHASE_LAUNCHES | PIC_FLAG_TIMING)) && nphase <= kWalkMaxPhases &&
+                      walk_ok(ctx, ndim, walls, count, push_smem);
+    if (!due.empty() && walk) {
+        // the sorts run inside the step walker: record their arguments, book the swap
+        for (int i : due) {
+            Run &r = ctx->runs[i];
+            for (int q = 0; q < r.d.nspecies; ++q) {
+                ctx->h_walk_sort[4 * i + q] = sort_args(ctx, r, r.sp[q]);
+                sort_done(r, r.sp[q]);
+            }
+            r.sorted = true;
+            r.since_sort = 0;
+        }
+    } else if (!due.empty()) {
+        // species q of every due run is sorted by one launch per sort phase
         KTimer t(ctx, PIC_KERNEL_SORT);
         for (int q = 0; q < maxsp; ++q) {
             int ns = 0;
@@ -858,10 +891,6 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         CK(cudaStreamSynchronize(s));
         ctx->multi_tiles_dirty = false;
     }
-    // when the next step sorts every run, this push counts their key histograms
-    bool count = true;
-    for (auto &r : ctx->runs)
-        if (!(r.since_sort + 1 >= r.sort_interval && r.t.lg[0] >= 0)) count = false;
     for (auto &r : ctx->runs) prepare_counts(ctx, r);
     for (int i = 0; i < nr; ++i) {
         Run &r = ctx->runs[i];
@@ -877,18 +906,17 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
                        sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->multi_fp, host_src(ctx, slot, soff, ctx->h_fp.data(), sizeof(FieldRunF) * nr),
                        sizeof(FieldRunF) * nr, cudaMemcpyHostToDevice, s));
-    const float dt = (float)ctx->runs[0].d.dt;
-    int max_smooth = 0;
-    for (auto &r : ctx->runs) max_smooth = std::max(max_smooth, r.smooth);
-    const int ndim = ctx->runs[0].d.ndim;
-    const bool walls = ctx->runs[0].g.bcx == 1;
-    const size_t push_smem = mixed_smem_bytes(ctx->runs[0].t, ndim);
-    const int nphase = 5 + (max_smooth > 0 ? 1 + max_smooth : 0);
-    if (!(ctx->flags & (PIC_FLAG_PHASE_LAUNCHES | PIC_FLAG_TIMING)) && nphase <= kWalkMaxPhases &&
-        walk_ok(ctx, ndim, walls, count, push_smem)) {
+    if (walk) {
         // the whole step in one persistent launch (walk.cu)
         WalkArgs w{};
         int np = 0;
+        if (!due.empty())
+            for (int q = 0; q < maxsp; ++q)
+                for (int k = S_ZERO; k <= S_GATHER; ++k) {
+                    w.species[np] = q;
+                    w.kind[np++] = k;
+                }
+        const int ph_push = np + 2;
         w.kind[np++] = W_B_HALF_E;
         w.kind[np++] = W_NODE;
         w.kind[np++] = W_PUSH;
@@ -902,8 +930,12 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         w.kind[np++] = W_B_HALF;
         w.kind[np++] = W_E_FX;
         const int cpi = walk_cells_per_item(ndim);
-        auto items = [&](int ph, const Run &r) -> int {
+        auto items = [&](int ph, int i) -> int {
+            const Run &r = ctx->runs[i];
             const long long ncell = (long long)r.g.nx * r.g.ny * r.g.nz;
+            if (w.kind[ph] <= S_GATHER)
+                return (is_due[i] && w.species[ph] < r.d.nspecies)
+                           ? walk_sort_items(ctx->h_walk_sort[4 * i + w.species[ph]], w.kind[ph], cpi) : 0;
             switch (w.kind[ph]) {
             case W_PUSH: return r.t.ntiles;
             case W_SMOOTH_FOLD: return r.smooth > 0 ? (int)((ncell + cpi - 1) / cpi) : 0;
@@ -911,29 +943,44 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
             default: return (int)((r.g.pcells + cpi - 1) / cpi);
             }
         };
-        int *prefix = ctx->h_walk.data(), *base = prefix + np * nr + 1;
+        int *prefix = ctx->h_walk.data(), *base = prefix + np * nr + 1, *order = base + nr * (np + 1);
+        // slots of a phase: runs by decreasing particles per tile (the longest push items first)
+        std::vector<double> load(nr, 0.0);
+        for (int i = 0; i < nr; ++i) {
+            const Run &r = ctx->runs[i];
+            for (int q = 0; q < r.d.nspecies; ++q) load[i] += (double)r.sp[q].n;
+            load[i] /= std::max(1, r.t.ntiles);
+            order[i] = i;
+        }
+        std::stable_sort(order, order + nr, [&](int a, int b) { return load[a] > load[b]; });
         int total = 0;
         for (int ph = 0; ph < np; ++ph)
-            for (int i = 0; i < nr; ++i) {
-                prefix[ph * nr + i] = total;
-                total += items(ph, ctx->runs[i]);
+            for (int k = 0; k < nr; ++k) {
+                prefix[ph * nr + k] = total;
+                total += items(ph, order[k]);
             }
         prefix[np * nr] = total;
         for (int i = 0; i < nr; ++i) {
             base[i * (np + 1)] = 0;
-            for (int ph = 0; ph < np; ++ph) base[i * (np + 1) + ph + 1] = base[i * (np + 1) + ph] + items(ph, ctx->runs[i]);
+            for (int ph = 0; ph < np; ++ph) base[i * (np + 1) + ph + 1] = base[i * (np + 1) + ph] + items(ph, i);
         }
         // test hook: the push of run 0 waits for an item that does not exist
-        if (ctx->flags & PIC_FLAG_INJECT_STALL) base[2] += 1;
-        const size_t tab = sizeof(int) * ((size_t)np * nr + 1 + (size_t)nr * (np + 1));
+        if (ctx->flags & PIC_FLAG_INJECT_STALL) base[ph_push] += 1;
+        const size_t tab = sizeof(int) * ((size_t)np * nr + 1 + (size_t)nr * (np + 2));
         CK(cudaMemcpyAsync(ctx->walk_tab, host_src(ctx, slot, soff, ctx->h_walk.data(), tab), tab,
                            cudaMemcpyHostToDevice, s));
+        if (!due.empty())
+            CK(cudaMemcpyAsync(ctx->walk_sort_dev,
+                               host_src(ctx, slot, soff, ctx->h_walk_sort.data(), sizeof(SortArgs) * 4 * nr),
+                               sizeof(SortArgs) * 4 * nr, cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(ctx->walk_ctl, 0, sizeof(int) * (2 + nr), s));
+        w.sort = ctx->walk_sort_dev;
         w.push = ctx->multi_args;
         w.fe = ctx->multi_fe;
         w.fp = ctx->multi_fp;
         w.prefix = ctx->walk_tab;
         w.base = ctx->walk_tab + np * nr + 1;
+        w.order = w.base + nr * (np + 1);
         w.head = ctx->walk_ctl;
         w.abort = ctx->walk_ctl + 1;
         w.done = ctx->walk_ctl + 2;
@@ -1187,7 +1234,7 @@ pic_status capture_graph(pic_ctx *ctx) {
         auto up = [a](size_t b) { return (b + a - 1) & ~(a - 1); };
         const size_t stride = up(sizeof(MixedStepArgs) * nr) + 2 * up(sizeof(FieldRunF) * nr) +
                               maxsp * (up(sizeof(SortArgs) * nr) + up(sizeof(int) * 4 * (nr + 1))) +
-                              up(sizeof(int) * walk_tab_ints(nr));
+                              up(sizeof(int) * walk_tab_ints(nr)) + up(sizeof(SortArgs) * 4 * nr);
         if (ctx->gstage_bytes < stride * P) {
             if (ctx->gstage) cudaFreeHost(ctx->gstage);
             ctx->gstage = nullptr;
@@ -1298,12 +1345,15 @@ pic_status pic_init(const pic_run_desc *runs, int nruns, const pic_opts *opts, p
         ctx->walk_tab = (int *)dev_alloc(ctx, sizeof(int) * walk_tab_ints(nruns));
         ctx->walk_ctl = (int *)dev_alloc(ctx, sizeof(int) * (2 + nruns));
         ctx->h_walk.resize(walk_tab_ints(nruns));
+        ctx->walk_sort_dev = (SortArgs *)dev_alloc(ctx, sizeof(SortArgs) * 4 * nruns);
+        ctx->h_walk_sort.assign(4 * (size_t)nruns, SortArgs{});
         ctx->sort_args_dev = (SortArgs *)dev_alloc(ctx, sizeof(SortArgs) * nruns);
         ctx->sort_prefix_dev = (int *)dev_alloc(ctx, sizeof(int) * 4 * (nruns + 1));
         ctx->h_sort.resize(nruns);
         ctx->h_sort_prefix.resize(4 * (nruns + 1));
         if (!ctx->multi_args || !ctx->multi_fe || !ctx->multi_fp || !ctx->multi_tiles || !ctx->multi_blocks ||
-            !ctx->multi_counter || !ctx->sort_args_dev || !ctx->sort_prefix_dev || !ctx->walk_tab || !ctx->walk_ctl) {
+            !ctx->multi_counter || !ctx->sort_args_dev || !ctx->sort_prefix_dev || !ctx->walk_tab || !ctx->walk_ctl ||
+            !ctx->walk_sort_dev) {
             pic_destroy(ctx);
             return PIC_ENOMEM;
         }

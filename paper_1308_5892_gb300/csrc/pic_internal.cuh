@@ -289,13 +289,21 @@ size_t mixed_smem_bytes(const TileGeom &t, int ndim);
 // walk.cu: the persistent step of a mixed ensemble (one launch per step).
 // Phases of one step, in order; every item of phase ph of run r waits until all
 // items of run r in phases before ph are done.
-enum WalkPhase { W_B_HALF_E = 0, W_NODE, W_PUSH, W_SMOOTH_FOLD, W_SMOOTH_PASS, W_B_HALF, W_E_FX };
-constexpr int kWalkMaxPhases = 16;
+struct SortArgs;
+enum WalkPhase {
+    // the counting sort of one species (steps that sort)
+    S_ZERO = 0, S_HIST, S_SCAN_BLOCKS, S_SCAN_SUMS, S_SCAN_FINISH, S_RANK, S_ZERO_AFTER, S_GATHER,
+    // the main loop
+    W_B_HALF_E, W_NODE, W_PUSH, W_SMOOTH_FOLD, W_SMOOTH_PASS, W_B_HALF, W_E_FX
+};
+constexpr int kWalkMaxPhases = 32;
 struct WalkArgs {
     const MixedStepArgs *push;     // per run
     const FieldRunF *fe, *fp;      // per run: first b half advance (records the energies); other field phases
-    const int *prefix;             // [nphase * nruns + 1]: first queue item of (phase, run), phase-major
+    const SortArgs *sort;          // [nruns * 4]: run r, species q at 4 r + q (runs that sort this step)
+    const int *prefix;             // [nphase * nruns + 1]: first queue item of (phase, slot), phase-major
     const int *base;               // [nruns * (nphase + 1)]: items of run r in the phases before each phase
+    const int *order;              // [nruns]: run of each slot of a phase (runs with the longest items first)
     int *head;                     // queue counter (zero before the launch)
     int *abort;                    // set when a wait runs out (zero before the launch)
     int *done;                     // [nruns] items of each run done (zero before the launch)
@@ -304,10 +312,13 @@ struct WalkArgs {
     int cells_per_item;            // cells of one field or smoothing item
     int kind[kWalkMaxPhases];      // WalkPhase of each phase
     int pass[kWalkMaxPhases];      // smoothing pass of a W_SMOOTH_PASS phase
+    int species[kWalkMaxPhases];   // species of a sort phase
     float h, dt;                   // h = dt/2 (half advances of b)
     long long wait_ns;             // bound of one wait (device global timer, ns)
 };
 int walk_cells_per_item(int ndim);
+// Items of sort phase `kind` of one species' sort in the walker.
+int walk_sort_items(const SortArgs &a, int kind, int cells_per_item);
 // Can the walker run a step with this push shared memory on this device?
 bool walk_fits(int ndim, bool walls, bool count, size_t push_smem);
 void launch_walk(const WalkArgs &w, int ndim, bool walls, bool count, size_t push_smem, cudaStream_t s);

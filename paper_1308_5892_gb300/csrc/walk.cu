@@ -1,20 +1,26 @@
 // walk.cu -- the persistent step of a mixed ensemble: one launch runs every
-// phase of one step of every run (main loop of App. A.3.1): b half advance
-// with the energy record, node-averaged fields, gather-push-deposit, the
-// optional current smoothing (step 10), b half advance, e advance with the
-// folded current.
+// phase of one step of every run: on the steps that re-sort a run, the phases
+// of the counting sort of each species (key histogram unless the previous push
+// counted it, block scans, rank, gather), then the main loop of App. A.3.1:
+// b half advance with the energy record, node-averaged fields,
+// gather-push-deposit, the optional current smoothing (step 10), b half
+// advance, e advance with the folded current.
 //
-// Work queue.  The items of phase ph of run r are the tiles of the run (push)
-// or chunks of cells_per_item cells (field and smoothing phases).  The queue
-// order is phase-major, runs in order inside a phase, and resident CTAs take
-// items from one counter.  Before an item of phase ph of run r starts, every
-// item of run r in the phases before ph must be done: thread 0 waits until the
-// run's done counter reaches that count (base[r][ph]).  Every item it waits on
-// lies earlier in the queue and was taken by a CTA that is running, so the
-// earliest unfinished item never waits and the walk progresses whatever the
-// number of resident CTAs.  Runs never wait on each other: while the tiles of
-// a large run are being pushed, the field phases of runs that are done go on,
-// so no phase ends with the GPU idle behind its slowest run.
+// Work queue.  The items of phase ph of run r are the tiles of the run (push,
+// and parts of the old layout's tiles for the sort's histogram and rank),
+// chunks of cells_per_item cells or keys (field, smoothing, zeroing and
+// scan-finish phases), scan blocks of 4096 keys, or gather chunks of 4096
+// particles.  The queue order is phase-major; inside a phase the runs with the
+// most particles per tile come first, so the longest items do not start last.
+// Resident CTAs take items from one counter.  Before an item of phase ph of
+// run r starts, every item of run r in the phases before ph must be done:
+// thread 0 waits until the run's done counter reaches that count
+// (base[r][ph]).  Every item it waits on lies earlier in the queue and was
+// taken by a CTA that is running, so the earliest unfinished item never waits
+// and the walk progresses whatever the number of resident CTAs.  Runs never
+// wait on each other: while the tiles of a large run are being pushed, the
+// field phases of runs that are done go on, so no phase ends with the GPU idle
+// behind its slowest run.
 //
 // Bounded waits.  A wait that runs out (wait_ns of the device's global timer)
 // sets ERR_TIMEOUT and the abort flag; every later item then skips its work and
@@ -31,10 +37,13 @@
 // Every item runs the same per-cell and per-tile bodies as the phase launches
 // (field_cells.cuh, smooth_cells.cuh, push_tile.cuh), so the fields, currents
 // and particles are bitwise those of one launch per phase.
+#include <algorithm>
+
 #define PIC_COHERENT_LOADS 1
 #include "field_cells.cuh"
 #include "push_tile.cuh"
 #include "smooth_cells.cuh"
+#include "sort_cells.cuh"
 
 namespace pic {
 
@@ -117,24 +126,72 @@ __device__ void field_item(const WalkArgs &w, int kind, int pass, const FieldRun
     }
 }
 
+// Items per old tile of the sort's histogram and rank phases: about 32768
+// particles each, at most 8 (a tile holds up to hundreds of thousands of
+// particles; shorter items balance the walk, fewer items cost less queueing).
+__host__ __device__ inline int walk_tile_parts(const SortArgs &a) {
+    const long long per_tile = a.n / (a.t.ntiles > 0 ? a.t.ntiles : 1);
+    const long long p = (per_tile + 32767) / 32768;
+    return (int)(p < 1 ? 1 : (p > 8 ? 8 : p));
+}
+
+// One item of a sort phase: block `local` of the `nitems` blocks of that phase
+// of species q's sort (sh: 33 ints of scratch for the scans).
+template <int NDIM, int THREADS>
+__device__ void sort_item(const SortArgs &a, int kind, int local, int nitems, int *sh) {
+    const long long nkeys = nkeys_of(a);
+    if (kind == S_ZERO || kind == S_ZERO_AFTER) {
+        zero_body(a.counts, nkeys, local, nitems);
+    } else if (kind == S_HIST) {
+        const SrcWalk sw{a.old_tile_start, a.n, local, nitems, walk_tile_parts(a)};
+        histogram_body<NDIM, 8>(a, sw, nkeys);
+    } else if (kind == S_SCAN_BLOCKS) {
+        scan_blocks_body<THREADS>(a.counts, a.offsets, a.block_sums, nkeys, local, sh);
+    } else if (kind == S_SCAN_SUMS) {
+        scan_sums_body<THREADS>(a.block_sums, scan_blocks(a), sh);
+    } else if (kind == S_SCAN_FINISH) {
+        scan_finish_body(a, nkeys, local, nitems);
+    } else if (kind == S_RANK) {
+        const SrcWalk sw{a.old_tile_start, a.n, local, nitems, walk_tile_parts(a)};
+        rank_body<NDIM, 8>(a, sw, nkeys);
+    } else {
+        // fewer warps per SM than the sort's own gather launch: every array per
+        // read of the permutation, more loads in flight per thread
+        gather_all_body<NDIM, THREADS, 4>(a.src, a.dst, a.n, a.perm, local);
+    }
+}
+
 template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 __global__ void __launch_bounds__(THREADS, MINB) k_walk(const __grid_constant__ WalkArgs w) {
     __shared__ int item_sh, go_sh;
+    __shared__ int scan_sh[33];
+    __shared__ __align__(16) SortArgs sort_sh;
     __shared__ __align__(128) MixedStepArgs args_sh;
     __shared__ __align__(16) FieldRunF fr_sh;
     const int nslot = w.nphase * w.nruns;
+    __shared__ int slot_sh;
+    if (threadIdx.x == 0) slot_sh = 0;
     for (;;) {
-        if (threadIdx.x == 0) item_sh = atomicAdd(w.head, 1);
+        if (threadIdx.x == 0) {
+            const int item = atomicAdd(w.head, 1);
+            item_sh = item;
+            // (phase, slot) of the item: the last slot whose first item is <= item.
+            // A CTA's items increase, so the previous slot bounds the search.
+            int lo = slot_sh;
+            if (item < w.total && !(w.prefix[lo] <= item && item < w.prefix[lo + 1])) {
+                int hi = nslot;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (w.prefix[mid] <= item) lo = mid; else hi = mid;
+                }
+            }
+            slot_sh = lo;
+        }
         __syncthreads();
         const int item = item_sh;
         if (item >= w.total) break;
-        // (phase, run) of the item: the last slot whose first item is <= item
-        int lo = 0, hi = nslot;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (w.prefix[mid] <= item) lo = mid; else hi = mid;
-        }
-        const int ph = lo / w.nruns, r = lo - ph * w.nruns;
+        const int lo = slot_sh;
+        const int ph = lo / w.nruns, r = w.order[lo - ph * w.nruns];
         const int local = item - w.prefix[lo];
         const int kind = w.kind[ph];
         if (threadIdx.x == 0) {
@@ -143,7 +200,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_walk(const __grid_constant__ 
         }
         __syncthreads();
         if (go_sh) {
-            if (kind == W_PUSH) {
+            if (kind <= S_GATHER) {
+                const int *src = reinterpret_cast<const int *>(w.sort + 4 * r + w.species[ph]);
+                int *dst = reinterpret_cast<int *>(&sort_sh);
+                for (int q = threadIdx.x; q < (int)(sizeof(SortArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
+                __syncthreads();
+                sort_item<NDIM, THREADS>(sort_sh, kind, local, w.prefix[lo + 1] - w.prefix[lo], scan_sh);
+            } else if (kind == W_PUSH) {
                 const int *src = reinterpret_cast<const int *>(w.push + r);
                 int *dst = reinterpret_cast<int *>(&args_sh);
                 for (int q = threadIdx.x; q < (int)(sizeof(MixedStepArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
@@ -212,8 +275,24 @@ bool fits_dim(bool walls, bool count, size_t smem) {
 
 }  // namespace
 
-// Field items of 8 cells per thread: 2048 cells (2D, 256 threads), 4096 (3D, 512 threads).
-int walk_cells_per_item(int ndim) { return ndim == 3 ? 4096 : 2048; }
+// Field items of 32 cells per thread: 8192 cells (2D, 256 threads), 16384 (3D, 512 threads).
+int walk_cells_per_item(int ndim) { return ndim == 3 ? 16384 : 8192; }
+
+int walk_sort_items(const SortArgs &a, int kind, int cpi) {
+    const long long nkeys = nkeys_of(a);
+    auto chunks = [](long long n, long long per) { return (int)std::max<long long>(1, (n + per - 1) / per); };
+    switch (kind) {
+    case S_ZERO: return a.counted ? 0 : chunks(nkeys, cpi);
+    case S_HIST: return (a.counted || a.n == 0) ? 0 : (a.old_tile_start ? a.t.ntiles * walk_tile_parts(a) : chunks(a.n, cpi));
+    case S_SCAN_BLOCKS: return scan_blocks(a);
+    case S_SCAN_SUMS: return 1;
+    case S_SCAN_FINISH: return chunks(nkeys, cpi);
+    case S_RANK: return a.n == 0 ? 0 : (a.old_tile_start ? a.t.ntiles * walk_tile_parts(a) : chunks(a.n, cpi));
+    case S_ZERO_AFTER: return chunks(nkeys, cpi);
+    case S_GATHER: return a.n == 0 ? 0 : chunks(a.n, kGatherChunk);
+    default: return 0;
+    }
+}
 
 bool walk_fits(int ndim, bool walls, bool count, size_t push_smem) {
     return ndim == 3 ? fits_dim<3, 512, 1>(walls, count, push_smem) : fits_dim<2, 256, 2>(walls, count, push_smem);

@@ -164,13 +164,13 @@ def _random_ensemble(runs, bc, seed0):
 
 @pytest.mark.parametrize("walls", [False, True])
 def test_step_walker_equals_phase_launches_bitwise(walls):
-    """The step walker (every phase of every run in one persistent launch, with
-    per-run dependencies) and one batched launch per phase advance the same
-    uneven ensemble to bitwise the same fields and particles: 14 steps with
-    re-sorts every 4 steps, graph replay on, members with 1 and 2 smoothing
-    passes in the periodic case, conducting x-walls in the other.  The walker
-    queues one kernel launch per step where the phase launches queue five or
-    more; the energy histories agree to 1e-6 (the kinetic energy is summed in
+    """The step walker (every phase of every run in one persistent launch, the
+    re-sorts included, with per-run dependencies) and one batched launch per
+    phase advance the same uneven ensemble to bitwise the same fields and
+    particles: 14 steps with re-sorts every 4 steps, graph replay on, members
+    with 1 and 2 smoothing passes in the periodic case, conducting x-walls in
+    the other.  The walker queues one kernel launch per step where the phase
+    launches queue five or more, and 16 more on a step that sorts; the energy histories agree to 1e-6 (the kinetic energy is summed in
     FP32 per block of particles, whose order inside a cell the sort's atomics
     set)."""
     runs = WALL_RUNS if walls else ORACLE_RUNS
@@ -193,7 +193,7 @@ def test_step_walker_equals_phase_launches_bitwise(walls):
         # the order of the particles inside a cell (set by the sort's atomics) changes
         # the FP32 partial sums of the kinetic energy at the 1e-8 level
         np.testing.assert_allclose(hw[r], hp[r], rtol=1e-6, atol=0)
-    assert lw < lp, (lw, lp)
+    assert lw == 1 and lp >= 5, (lw, lp)
 
 
 def test_step_walker_bounded_wait_reports_timeout():
