@@ -258,9 +258,10 @@ pic_status pic_load_maxwell_juttner(pic_ctx *ctx, int run, int species, double p
  * direct launches.
  * Ensembles (nruns > 1, PIC_MIXED): unless PIC_FLAG_PHASE_LAUNCHES or
  * PIC_FLAG_TIMING, each step is one persistent launch (the step walker: a work
- * queue of (phase, run, tile or cell chunk) items with per-run dependencies and
- * bounded waits), plus the batched sort launches on the steps that sort; the
- * fields and particles are bitwise those of the phase launches. */
+ * queue of (phase, run, item) items with per-run dependencies and bounded
+ * waits, covering the re-sorts that are due, the field updates, the push and
+ * the current smoothing); the fields and particles are bitwise those of the
+ * launches per phase. */
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
 /* Wait for queued work and report the device-side error flag. */
