@@ -452,10 +452,10 @@ FP64_INST_PER_PARTICLE = {3: 274.0, 2: 170.0}
 MIXED_FP32_FLOPS_PER_PARTICLE = {3: 331.8}
 # DRAM bytes (read + written) per particle-step of the 3D push kernel, from one
 # ncu capture of the same kernel and tiling (16x8x4, sort interval 3) on the
-# 64^3 case (profiles/push_mixed_thermal3d_64.md: 916.9 MB for 16,777,216
+# 64^3 case (profiles/push_mixed_thermal3d_64.md: 917.2 MB for 16,777,216
 # particles), scaled to a launch by the particles it processes.  None where no
 # capture exists.
-PUSH_TRAFFIC_B_PER_PARTICLE = {3: 916.9e6 / 16777216}
+PUSH_TRAFFIC_B_PER_PARTICLE = {3: 917.2e6 / 16777216}
 PUSH_TRAFFIC_TILING = {3: ([16, 8, 4], 3)}   # (tile, sort interval) of that capture
 
 
