@@ -39,6 +39,9 @@ WORKLOADS = {
     "ensemble256": dict(name="256 independent 2D3V thermal pair plasmas, grids 32^2..256^2, ppc/species in {4..256}, "
                              "theta in [0.01, 1]", ndim=2, nx=0, ny=0, nz=1, ppc=0, theta=0.0, n_x=0.0, rho_sp0=0.0,
                         dt=0.5, ensemble=256),
+    "ensemble16": dict(name="16 independent 2D3V thermal pair plasmas (the first 16 runs of ensemble256; profiling "
+                            "size)", ndim=2, nx=0, ny=0, nz=1, ppc=0, theta=0.0, n_x=0.0, rho_sp0=0.0, dt=0.5,
+                       ensemble=16),
     "thermal2d_64": dict(name="2D3V thermal pair plasma 64^2, 16 ppc/species, theta=0.1", ndim=2, nx=64, ny=64, nz=1,
                          ppc=16, theta=0.1, n_x=0.1 ** -0.5, rho_sp0=32.0, dt=0.5),
 }

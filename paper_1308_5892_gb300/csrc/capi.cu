@@ -845,7 +845,18 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
     const int nphase = (due.empty() ? 0 : 8 * maxsp) + 5 + (max_smooth > 0 ? 1 + max_smooth : 0);
     const bool walk = !(ctx->flags & (PIC_FLAG_PHASE_LAUNCHES | PIC_FLAG_TIMING)) && nphase <= kWalkMaxPhases &&
                       walk_ok(ctx, ndim, walls, count, push_smem);
-    if (!due.empty() && walk) {
+    // The walker sorts too unless one run holds more than a quarter of the particles: that run's
+    // sort alone then sets the time, and its own launches per phase (more warps per SM for the
+    // latency-bound gather and rank) finish it sooner.
+    long long most = 0, all = 0;
+    for (int i : due) {
+        long long n = 0;
+        for (int q = 0; q < ctx->runs[i].d.nspecies; ++q) n += ctx->runs[i].sp[q].n;
+        most = std::max(most, n);
+        all += n;
+    }
+    const bool walk_sort = walk && most * 4 <= all;
+    if (!due.empty() && walk_sort) {
         // the sorts run inside the step walker: record their arguments, book the swap
         for (int i : due) {
             Run &r = ctx->runs[i];
@@ -910,7 +921,7 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         // the whole step in one persistent launch (walk.cu)
         WalkArgs w{};
         int np = 0;
-        if (!due.empty())
+        if (!due.empty() && walk_sort)
             for (int q = 0; q < maxsp; ++q)
                 for (int k = S_ZERO; k <= S_GATHER; ++k) {
                     w.species[np] = q;
@@ -969,7 +980,7 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         const size_t tab = sizeof(int) * ((size_t)np * nr + 1 + (size_t)nr * (np + 2));
         CK(cudaMemcpyAsync(ctx->walk_tab, host_src(ctx, slot, soff, ctx->h_walk.data(), tab), tab,
                            cudaMemcpyHostToDevice, s));
-        if (!due.empty())
+        if (!due.empty() && walk_sort)
             CK(cudaMemcpyAsync(ctx->walk_sort_dev,
                                host_src(ctx, slot, soff, ctx->h_walk_sort.data(), sizeof(SortArgs) * 4 * nr),
                                sizeof(SortArgs) * 4 * nr, cudaMemcpyHostToDevice, s));
