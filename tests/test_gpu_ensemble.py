@@ -150,12 +150,18 @@ def test_ensemble_members_match_oracle(walls):
 
 
 def _random_ensemble(runs, bc, seed0):
+    """runs: (nx, ny, ppc, amp, smoothing passes) for 2D3V members, (nx, ny, nz, ppc, amp,
+    smoothing passes) for 3D3V members."""
     descs, states = [], []
-    for r, (nx, ny, ppc, amp, sm) in enumerate(runs):
-        arr = synth.random_state_arrays(seed0 + r, 2, nx, ny, 1, ppc=ppc, spread=0.6, amp_e=amp, amp_b=amp,
+    for r, run in enumerate(runs):
+        if len(run) == 5:
+            (nx, ny, ppc, amp, sm), nz, ndim = run, 1, 2
+        else:
+            (nx, ny, nz, ppc, amp, sm), ndim = run, 3
+        arr = synth.random_state_arrays(seed0 + r, ndim, nx, ny, nz, ppc=ppc, spread=0.6, amp_e=amp, amp_b=amp,
                                         colocate=False)
         n = arr["species"][0]["pos"].shape[1]
-        descs.append(pic.run_desc(2, nx, ny, 1, 2.0, 8.0, 0.5, [(-1.0, 1.0, n), (1.0, 1.0, n)], bc=bc,
+        descs.append(pic.run_desc(ndim, nx, ny, nz, 2.0, 8.0, 0.5, [(-1.0, 1.0, n), (1.0, 1.0, n)], bc=bc,
                                   smooth_passes=sm))
         states.append((np.concatenate([arr["e"], arr["b"]]), [np.concatenate([sp["pos"], sp["u"]])
                                                               for sp in arr["species"]]))
@@ -167,15 +173,18 @@ BALANCED_RUNS = [(40, 40, 6, 0.03, 0), (44, 36, 6, 0.05, 1), (36, 44, 6, 0.04, 0
                  (32, 48, 6, 0.02, 0), (40, 38, 6, 0.04, 0)]
 BALANCED_WALL_RUNS = [(40, 32, 5, 0.03, 0), (36, 36, 5, 0.05, 0), (32, 40, 5, 0.02, 0), (38, 34, 5, 0.04, 0),
                       (34, 38, 5, 0.03, 0)]
+BALANCED_3D_RUNS = [(16, 16, 12, 3, 0.03, 0), (12, 16, 16, 3, 0.05, 1), (16, 12, 16, 3, 0.04, 0),
+                    (14, 14, 14, 3, 0.05, 0), (16, 16, 10, 3, 0.02, 0)]
 
 
-@pytest.mark.parametrize("case", ["balanced", "balanced_walls", "dominated"])
+@pytest.mark.parametrize("case", ["balanced", "balanced_walls", "balanced_3d", "dominated"])
 def test_step_walker_equals_phase_launches_bitwise(case):
     """The step walker (every phase of every run in one persistent launch,
     with per-run dependencies) and one batched launch per phase advance the
     same uneven ensemble to bitwise the same fields and particles: 14 steps
     with re-sorts every 4 steps, graph replay on.  In the balanced ensembles
-    (periodic, with members of 1 and 2 smoothing passes; conducting x-walls)
+    (periodic, with members of 1 and 2 smoothing passes; conducting x-walls;
+    3D3V members, one of which also matches its single-run context bitwise)
     the walker runs the re-sorts too and queues one kernel launch per step; in
     the ensemble where one run holds over a quarter of the particles the
     sorts run as launches per phase and the walker does the rest.  The phase
@@ -183,7 +192,7 @@ def test_step_walker_equals_phase_launches_bitwise(case):
     (the kinetic energy is summed in FP32 per block of particles, whose order
     inside a cell the sort's atomics set)."""
     runs, walls = {"balanced": (BALANCED_RUNS, False), "balanced_walls": (BALANCED_WALL_RUNS, True),
-                   "dominated": (ORACLE_RUNS, False)}[case]
+                   "balanced_3d": (BALANCED_3D_RUNS, False), "dominated": (ORACLE_RUNS, False)}[case]
     descs, states = _random_ensemble(runs, (1, 0, 0) if walls else (0, 0, 0), 700)
     out = []
     for flags in (0, pic.PIC_FLAG_PHASE_LAUNCHES):
@@ -204,6 +213,15 @@ def test_step_walker_equals_phase_launches_bitwise(case):
         # the FP32 partial sums of the kinetic energy at the 1e-8 level
         np.testing.assert_allclose(hw[r], hp[r], rtol=1e-6, atol=0)
     assert lp >= 5 and (lw == 1 if case != "dominated" else 1 <= lw < lp), (lw, lp)
+    if case == "balanced_3d":
+        # a 3D member advanced alone (one CTA per tile, separate kernels) gives the same bits
+        with pic.Context([descs[1]], precision=pic.PIC_MIXED, sort_interval=4) as one:
+            one.set_state(0, *states[1])
+            one.step(14)
+            f, p, _ = one.get_state(0)
+        assert np.array_equal(f, walk[1][0])
+        for s in range(2):
+            assert np.array_equal(p[s], walk[1][1][s])
 
 
 def test_step_walker_bounded_wait_reports_timeout():
