@@ -30,13 +30,16 @@
 // Ordering.  A finished item is published by a fence and an atomic add on the
 // run's counter (thread 0, after the CTA barrier); the waiter reads the
 // counter with acquire semantics and fences before the CTA barrier that
-// releases its threads.  The push stages the node fields with coalesced loads
-// here, not with TMA: they were written by other CTAs of the same launch
-// through the generic proxy.
+// releases its threads.  Items read arrays that other CTAs of the same launch
+// wrote (b, the node fields, the current, the sort's counts, offsets and
+// permutation), so this translation unit compiles the bodies with plain loads
+// (PIC_COHERENT_LOADS) instead of the read-only data path, and the push stages
+// the node fields with coalesced loads instead of TMA (they were written
+// through the generic proxy).
 //
 // Every item runs the same per-cell and per-tile bodies as the phase launches
-// (field_cells.cuh, smooth_cells.cuh, push_tile.cuh), so the fields, currents
-// and particles are bitwise those of one launch per phase.
+// (field_cells.cuh, smooth_cells.cuh, sort_cells.cuh, push_tile.cuh), so the
+// fields, currents and particles are bitwise those of one launch per phase.
 #include <algorithm>
 
 #define PIC_COHERENT_LOADS 1
