@@ -254,3 +254,32 @@ def test_step_walker_bounded_wait_reports_timeout():
         assert np.array_equal(got[r][0], want[r][0]), r
         for s in range(2):
             assert np.array_equal(got[r][1][s], want[r][1][s]), (r, s)
+
+
+def test_step_walker_with_empty_species_and_runs():
+    """Degenerate members in a walker ensemble: one run's positron species is
+    empty (capacity 0) and another run holds no particles at all.  Over 9
+    steps with re-sorts every 2 steps the walker and the launches per phase
+    give bitwise the same fields and particles, and the empty species stay
+    empty.  No run holds a quarter of the particles, so the walker sorts too."""
+    runs = BALANCED_RUNS
+    descs, states = _random_ensemble(runs, (0, 0, 0), 800)
+    descs[1].species[1].capacity = 0
+    states[1] = (states[1][0], [states[1][1][0], np.zeros((6, 0))])
+    for q in range(2):
+        descs[3].species[q].capacity = 0
+    states[3] = (states[3][0], [np.zeros((6, 0)), np.zeros((6, 0))])
+    out = []
+    for flags in (0, pic.PIC_FLAG_PHASE_LAUNCHES):
+        with pic.Context(descs, precision=pic.PIC_MIXED, sort_interval=2, flags=flags) as ens:
+            for r, (fields, parts) in enumerate(states):
+                ens.set_state(r, fields, parts)
+            ens.step(9)
+            out.append([ens.get_state(r) for r in range(len(runs))])
+    walk, phase = out
+    for r in range(len(runs)):
+        assert np.array_equal(walk[r][0], phase[r][0]), r
+        for s in range(2):
+            assert np.array_equal(walk[r][1][s], phase[r][1][s]), (r, s)
+    assert walk[1][1][1].shape == (6, 0) and walk[3][1][0].shape == (6, 0) and walk[3][1][1].shape == (6, 0)
+    assert np.all(np.isfinite(walk[3][0]))
