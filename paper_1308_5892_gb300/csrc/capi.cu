@@ -1003,7 +1003,7 @@ pic_status step_multi(pic_ctx *ctx, int slot) {
         w.h = 0.5f * dt;
         w.dt = dt;
         w.wait_ns = (ctx->flags & PIC_FLAG_INJECT_STALL) ? 20000000LL : 2000000000LL;
-        launch_walk(w, ndim, walls, count, push_smem, s);
+        launch_walk(w, ndim, walls, count, push_smem, fixed_tile_code(ctx->runs[0].t, ndim), s);
         CK(cudaGetLastError());
         if (count)
             for (auto &r : ctx->runs)

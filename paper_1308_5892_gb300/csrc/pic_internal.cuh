@@ -159,6 +159,25 @@ struct TileGeom {
     int lg[3];       // log2 T per axis when every T is a power of two, else -1
 };
 
+// Tile shapes that the push is also compiled for with a fixed geometry (the
+// autotuner's choices for the 128^3 and 1024^2 workloads), so that node and
+// current-slot offsets become immediates, by code: 1: 3D 16x8x4, halo 3; 2: 2D
+// 16x16, halo 4.  Code 0: the geometry is read at run time.
+struct FixedTile {
+    int T0, T1, T2, H;
+};
+__host__ __device__ constexpr FixedTile fixed_tile(int code) {
+    return code == 1 ? FixedTile{16, 8, 4, 3} : code == 2 ? FixedTile{16, 16, 1, 4} : FixedTile{0, 0, 0, 0};
+}
+// Code of a tile geometry (0 when it has no fixed form).
+inline int fixed_tile_code(const TileGeom &t, int ndim) {
+    for (int c = 1; c <= 2; ++c) {
+        const FixedTile f = fixed_tile(c);
+        if ((ndim == 3) == (f.T2 > 1) && t.T[0] == f.T0 && t.T[1] == f.T1 && t.T[2] == f.T2 && t.H == f.H) return c;
+    }
+    return 0;
+}
+
 // Sort key of a cell: tile index * cells_per_tile + index inside the tile
 // (tiles with power-of-two sides only, t.lg[0] >= 0).
 __host__ __device__ inline int tile_key_pow2(const TileGeom &t, int i, int j, int k) {
@@ -321,7 +340,9 @@ int walk_cells_per_item(int ndim);
 int walk_sort_items(const SortArgs &a, int kind, int cells_per_item);
 // Can the walker run a step with this push shared memory on this device?
 bool walk_fits(int ndim, bool walls, bool count, size_t push_smem);
-void launch_walk(const WalkArgs &w, int ndim, bool walls, bool count, size_t push_smem, cudaStream_t s);
+// tile_code: fixed_tile_code of the runs' (common) tile geometry
+void launch_walk(const WalkArgs &w, int ndim, bool walls, bool count, size_t push_smem, int tile_code,
+                 cudaStream_t s);
 // dynamic shared memory a push CTA may use (227 KB per block, less the kernels' static shared memory)
 constexpr size_t kMaxPushSmem = 224 * 1024;
 

@@ -10,17 +10,18 @@ namespace pic {
 namespace {
 
 // One CTA per tile of one run; WALLS: conducting walls in x (a separate
-// instantiation keeps their register cost out of the periodic kernel).
-template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
+// instantiation keeps their register cost out of the periodic kernel); CT: the
+// fixed tile geometry code (fixed_tile), 0 for the run-time geometry.
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST, int CT>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed(const __grid_constant__ MixedStepArgs a) {
-    push_tile<NDIM, THREADS, WALLS, HIST>(a, blockIdx.x, &a);
+    push_tile<NDIM, THREADS, WALLS, HIST, CT>(a, blockIdx.x, &a);
 }
 
 // Persistent form for a batch of independent runs of uneven size: resident
 // CTAs take (run, tile) work items from one counter until all tiles of all
 // runs are done, so small runs do not leave most of the GPU idle.
 // tile_prefix[r] is the number of tiles of runs 0..r-1.
-template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST, int CT>
 __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedStepArgs *runs, const int *tile_prefix,
                                                                     int nruns, int *counter) {
     __shared__ int item_sh;
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_push_mixed_multi(const MixedS
         int *dst = reinterpret_cast<int *>(&args_sh);
         for (int q = threadIdx.x; q < (int)(sizeof(MixedStepArgs) / sizeof(int)); q += THREADS) dst[q] = src[q];
         __syncthreads();
-        push_tile<NDIM, THREADS, WALLS, HIST>(args_sh, item - tile_prefix[lo], runs + lo);
+        push_tile<NDIM, THREADS, WALLS, HIST, CT>(args_sh, item - tile_prefix[lo], runs + lo);
     }
 }
 
@@ -61,9 +62,31 @@ __global__ void k_half_back_mixed(Geom g, const float4 *nfA, const float2 *nfB, 
     }
 }
 
+// The kernel instance for a tile geometry code: the fixed form where one exists
+// for NDIM (periodic runs), else the run-time one.
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
+auto push_kernel(int ct) {
+    auto k = k_push_mixed<NDIM, THREADS, MINB, WALLS, HIST, 0>;
+    if constexpr (!WALLS && NDIM == 3) {
+        if (ct == 1) k = k_push_mixed<NDIM, THREADS, MINB, WALLS, HIST, 1>;
+    } else if constexpr (!WALLS) {
+        if (ct == 2) k = k_push_mixed<NDIM, THREADS, MINB, WALLS, HIST, 2>;
+    }
+    return k;
+}
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
+auto push_multi_kernel(int ct) {
+    auto k = k_push_mixed_multi<NDIM, THREADS, MINB, WALLS, HIST, 0>;
+    // (the 3D fixed form spills a few registers in this kernel: the run-time one is kept)
+    if constexpr (!WALLS && NDIM == 2) {
+        if (ct == 2) k = k_push_mixed_multi<NDIM, THREADS, MINB, WALLS, HIST, 2>;
+    }
+    return k;
+}
+
 template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 void launch_t(const MixedStepArgs &a, size_t smem, cudaStream_t s) {
-    auto k = k_push_mixed<NDIM, THREADS, MINB, WALLS, HIST>;
+    auto k = push_kernel<NDIM, THREADS, MINB, WALLS, HIST>(fixed_tile_code(a.t, NDIM));
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<a.t.ntiles, THREADS, smem, s>>>(a);
 }
@@ -86,9 +109,9 @@ void launch_half_back_mixed(const Geom &g, const float4 *nfA, const float2 *nfB,
 }
 
 template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
-void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem,
+void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem, int ct,
                     cudaStream_t s) {
-    auto k = k_push_mixed_multi<NDIM, THREADS, MINB, WALLS, HIST>;
+    auto k = push_multi_kernel<NDIM, THREADS, MINB, WALLS, HIST>(ct);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
@@ -100,21 +123,22 @@ void launch_multi_t(const MixedStepArgs *runs, const int *tile_prefix, int nruns
 
 template <int NDIM, int THREADS, int MINB>
 void launch_multi_dim(const MixedStepArgs *runs, const int *tile_prefix, int nruns, int *counter, size_t smem,
-                      bool walls, bool count, cudaStream_t s) {
+                      bool walls, bool count, int ct, cudaStream_t s) {
     if (walls) {
-        if (count) launch_multi_t<NDIM, THREADS, MINB, true, true>(runs, tile_prefix, nruns, counter, smem, s);
-        else launch_multi_t<NDIM, THREADS, MINB, true, false>(runs, tile_prefix, nruns, counter, smem, s);
+        if (count) launch_multi_t<NDIM, THREADS, MINB, true, true>(runs, tile_prefix, nruns, counter, smem, ct, s);
+        else launch_multi_t<NDIM, THREADS, MINB, true, false>(runs, tile_prefix, nruns, counter, smem, ct, s);
     } else {
-        if (count) launch_multi_t<NDIM, THREADS, MINB, false, true>(runs, tile_prefix, nruns, counter, smem, s);
-        else launch_multi_t<NDIM, THREADS, MINB, false, false>(runs, tile_prefix, nruns, counter, smem, s);
+        if (count) launch_multi_t<NDIM, THREADS, MINB, false, true>(runs, tile_prefix, nruns, counter, smem, ct, s);
+        else launch_multi_t<NDIM, THREADS, MINB, false, false>(runs, tile_prefix, nruns, counter, smem, ct, s);
     }
 }
 
 void launch_push_mixed_multi(const MixedStepArgs *runs_dev, const int *tile_prefix_dev, int nruns, int ndim,
                              const TileGeom &t, bool walls, bool count, int *counter, cudaStream_t s) {
     const size_t smem = mixed_smem_bytes(t, ndim);
-    if (ndim == 3) launch_multi_dim<3, 512, 1>(runs_dev, tile_prefix_dev, nruns, counter, smem, walls, count, s);
-    else launch_multi_dim<2, 256, 2>(runs_dev, tile_prefix_dev, nruns, counter, smem, walls, count, s);
+    const int ct = fixed_tile_code(t, ndim);
+    if (ndim == 3) launch_multi_dim<3, 512, 1>(runs_dev, tile_prefix_dev, nruns, counter, smem, walls, count, ct, s);
+    else launch_multi_dim<2, 256, 2>(runs_dev, tile_prefix_dev, nruns, counter, smem, walls, count, ct, s);
 }
 
 template <int NDIM, int THREADS, int MINB>

@@ -410,7 +410,8 @@ __host__ __device__ inline size_t node_b_offset(int nodes) { return ((size_t)nod
 
 // tmaps: the arguments' copy whose TMA descriptors are in parameter or global
 // memory (the multi-run kernel stages its arguments in shared memory).
-template <int NDIM, int THREADS, bool WALLS, bool HIST>
+// CT: fixed tile geometry code (fixed_tile), 0 for the run-time geometry.
+template <int NDIM, int THREADS, bool WALLS, bool HIST, int CT = 0>
 __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile, const MixedStepArgs *tmaps) {
     extern __shared__ __align__(128) float4 smem4[];
     __shared__ __align__(8) unsigned long long tma_bar;
@@ -427,6 +428,15 @@ __device__ __forceinline__ void push_tile(const MixedStepArgs &a, const int tile
     tc.sx = tc.Rx; tc.sxy = tc.Rx * tc.Ry;
     tc.nodes = tc.Rx * tc.Ry * tc.Rz;
     tc.H = T.H; tc.T0 = T.T[0]; tc.T1 = T.T[1]; tc.T2 = T.T[2];
+    if constexpr (CT != 0) {
+        // the same geometry as constants: offsets of nodes and current slots fold into immediates
+        constexpr FixedTile F = fixed_tile(CT);
+        constexpr int Rx = F.T0 + 2 * F.H, Ry = F.T1 + 2 * F.H, Rz = NDIM == 3 ? F.T2 + 2 * F.H : 1;
+        tc.x0 = tx * F.T0; tc.y0 = ty * F.T1; tc.z0 = NDIM == 3 ? tz * F.T2 : 0;
+        tc.Rx = Rx; tc.Ry = Ry; tc.Rz = Rz;
+        tc.sx = Rx; tc.sxy = Rx * Ry; tc.nodes = Rx * Ry * Rz;
+        tc.H = F.H; tc.T0 = F.T0; tc.T1 = F.T1; tc.T2 = F.T2;
+    }
     const int nodes = tc.nodes;
     float4 *nA = smem4;
     float2 *nB = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem4) + node_b_offset(nodes));

@@ -164,7 +164,7 @@ __device__ void sort_item(const SortArgs &a, int kind, int local, int nitems, in
     }
 }
 
-template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST, int CT>
 __global__ void __launch_bounds__(THREADS, MINB) k_walk(const __grid_constant__ WalkArgs w) {
     __shared__ int item_sh, go_sh;
     __shared__ int scan_sh[33];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_walk(const __grid_constant__ 
                 __syncthreads();
                 if (threadIdx.x == 0) args_sh.use_tma = 0;
                 __syncthreads();
-                push_tile<NDIM, THREADS, WALLS, HIST>(args_sh, local, w.push + r);
+                push_tile<NDIM, THREADS, WALLS, HIST, CT>(args_sh, local, w.push + r);
             } else {
                 const FieldRunF *fsrc = kind == W_B_HALF_E ? w.fe + r : w.fp + r;
                 const int *src = reinterpret_cast<const int *>(fsrc);
@@ -234,10 +234,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_walk(const __grid_constant__ 
     }
 }
 
+// The walker instance for a tile geometry code (fixed_tile): the fixed form where
+// one exists for NDIM (periodic runs), else the run-time one.
+template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
+auto walk_kernel(int ct) {
+    auto k = k_walk<NDIM, THREADS, MINB, WALLS, HIST, 0>;
+    // (the 3D fixed form spills a few registers in this kernel: the run-time one is kept)
+    if constexpr (!WALLS && NDIM == 2) {
+        if (ct == 2) k = k_walk<NDIM, THREADS, MINB, WALLS, HIST, 2>;
+    }
+    return k;
+}
+
 template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
 bool fits_t(size_t smem) {
     cudaFuncAttributes attr;
-    if (cudaFuncGetAttributes(&attr, k_walk<NDIM, THREADS, MINB, WALLS, HIST>) != cudaSuccess) {
+    // the fixed-geometry forms hold the same static shared memory
+    if (cudaFuncGetAttributes(&attr, k_walk<NDIM, THREADS, MINB, WALLS, HIST, 0>) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -248,8 +261,8 @@ bool fits_t(size_t smem) {
 }
 
 template <int NDIM, int THREADS, int MINB, bool WALLS, bool HIST>
-void launch_t(const WalkArgs &w, size_t smem, cudaStream_t s) {
-    auto k = k_walk<NDIM, THREADS, MINB, WALLS, HIST>;
+void launch_t(const WalkArgs &w, size_t smem, int ct, cudaStream_t s) {
+    auto k = walk_kernel<NDIM, THREADS, MINB, WALLS, HIST>(ct);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0, dev = 0, sms = 152;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem);
@@ -260,13 +273,13 @@ void launch_t(const WalkArgs &w, size_t smem, cudaStream_t s) {
 }
 
 template <int NDIM, int THREADS, int MINB>
-void launch_dim(const WalkArgs &w, bool walls, bool count, size_t smem, cudaStream_t s) {
+void launch_dim(const WalkArgs &w, bool walls, bool count, size_t smem, int ct, cudaStream_t s) {
     if (walls) {
-        if (count) launch_t<NDIM, THREADS, MINB, true, true>(w, smem, s);
-        else launch_t<NDIM, THREADS, MINB, true, false>(w, smem, s);
+        if (count) launch_t<NDIM, THREADS, MINB, true, true>(w, smem, ct, s);
+        else launch_t<NDIM, THREADS, MINB, true, false>(w, smem, ct, s);
     } else {
-        if (count) launch_t<NDIM, THREADS, MINB, false, true>(w, smem, s);
-        else launch_t<NDIM, THREADS, MINB, false, false>(w, smem, s);
+        if (count) launch_t<NDIM, THREADS, MINB, false, true>(w, smem, ct, s);
+        else launch_t<NDIM, THREADS, MINB, false, false>(w, smem, ct, s);
     }
 }
 
@@ -301,10 +314,11 @@ bool walk_fits(int ndim, bool walls, bool count, size_t push_smem) {
     return ndim == 3 ? fits_dim<3, 512, 1>(walls, count, push_smem) : fits_dim<2, 256, 2>(walls, count, push_smem);
 }
 
-void launch_walk(const WalkArgs &w, int ndim, bool walls, bool count, size_t push_smem, cudaStream_t s) {
+void launch_walk(const WalkArgs &w, int ndim, bool walls, bool count, size_t push_smem, int tile_code,
+                 cudaStream_t s) {
     if (w.total <= 0) return;
-    if (ndim == 3) launch_dim<3, 512, 1>(w, walls, count, push_smem, s);
-    else launch_dim<2, 256, 2>(w, walls, count, push_smem, s);
+    if (ndim == 3) launch_dim<3, 512, 1>(w, walls, count, push_smem, tile_code, s);
+    else launch_dim<2, 256, 2>(w, walls, count, push_smem, tile_code, s);
 }
 
 }  // namespace pic
